@@ -1,0 +1,126 @@
+/*
+ * Plain FP64 CPU oracle for decentralized ADMM tomography with quantized
+ * messages ("Distributed Tomographic Reconstruction with Quantization",
+ * arXiv 2410.06106).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it. The CUDA library never links,
+ * includes or calls anything here, and nothing here includes the CUDA
+ * library's headers.
+ *
+ * Geometry convention (the paper leaves it open, Sec. 2.1):
+ *   pixel (i, j) of an N x N image is the unit square centred at
+ *     x_j = j - (N-1)/2,  y_i = (N-1)/2 - i    (row 0 at the top, y up);
+ *   ray (a, b) is the line  x cos(theta_a) + y sin(theta_a) = t_b,
+ *     t_b = b - (B-1)/2,  unit detector spacing;
+ *   P[(a,b),(i,j)] = length of the intersection of that line with that
+ *     pixel (Eq. 2). A line lying exactly on the common edge of two pixels
+ *     gives each of them half of the edge length.
+ *
+ * All image / sinogram arrays are row-major and contiguous.
+ */
+#ifndef TOMO_ORACLE_H
+#define TOMO_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* number of OpenMP threads the oracle runs with */
+int orc_num_threads(void);
+
+/* cos/sin of each angle; multiples of pi/2 (within 1e-12 rad) are snapped to
+ * exact 0 / +-1. */
+void orc_trig(int n, const double* theta, double* c, double* s);
+
+/* Eq. 2 entry: length of the line {x c + y s = t} inside the unit square
+ * centred at (xc, yc), by clipping the line against the square. */
+double orc_chord(double c, double s, double t, double xc, double yc);
+
+/* Eq. 4, d = P u, for the angle rows aidx[0..nsel).
+ * img [batch][N][N], sino [batch][nsel][B]. */
+void orc_project(int N, int B, const double* c, const double* s, int nsel,
+                 const int32_t* aidx, int batch, const double* img, double* sino);
+
+/* transpose: img = P^T sino, same layouts */
+void orc_backproject(int N, int B, const double* c, const double* s, int nsel,
+                     const int32_t* aidx, int batch, const double* sino, double* img);
+
+/* single rays (ray_a[r], ray_b[r]) of P u; img [N][N] */
+void orc_project_rays(int N, int B, const double* c, const double* s, int nray,
+                      const int32_t* ray_a, const int32_t* ray_b,
+                      const double* img, double* out);
+
+/* single pixels pix[q] (flat index i*N+j) of P^T sino; sino [nsel][B] */
+void orc_backproject_pixels(int N, int B, const double* c, const double* s,
+                            int nsel, const int32_t* aidx, const double* sino,
+                            int npix, const int32_t* pix, double* out);
+
+/* ||P_sel||_2^2 by power iteration on P^T P from a seeded start vector */
+double orc_opnorm_sq(int N, int B, const double* c, const double* s, int nsel,
+                     const int32_t* aidx, int iters, uint64_t seed);
+
+/* splitmix64 output function (Steele, Lea & Flood 2014) and the counter key
+ * used for K-means initialisation of owner `owner`, slice `slice` at ADMM
+ * iteration `iter`. */
+uint64_t orc_mix64(uint64_t z);
+uint64_t orc_kmeans_key(uint64_t seed, int slice, int owner, int iter);
+
+/* Algorithm 5: scalar K-means quantizer of v[0..n). codes [n], cent [k],
+ * deq [n]; obj [iters+1] (nullable) receives the distortion after every
+ * assignment step. */
+void orc_kmeans(const float* v, int64_t n, int k, int iters, uint64_t key,
+                uint8_t* codes, float* cent, float* deq, double* obj);
+
+/* JPEG luminance table scaled to `quality` (IJG rule), natural order */
+void orc_jpeg_qtable(int quality, int32_t* qt);
+
+/* orthonormal 8x8 DCT-II and its inverse, FP64, natural order */
+void orc_dct8x8(const double* in, double* out);
+void orc_idct8x8(const double* in, double* out);
+
+/* JPEG-style codec of a rows x cols segment (both multiples of 8).
+ * coefs [rows/8][cols/8][64], lohi [2], deq [rows][cols].
+ * Returns the number of non-zero quantized coefficients. */
+int64_t orc_jpeg(const float* v, int rows, int cols, int quality,
+                 int16_t* coefs, float* lohi, float* deq);
+
+/* Relay tables of the message graph: dist[s*M+m] = hop distance from owner s
+ * to node m (-1 if unreachable), first[s*M+m] = the neighbour of s on the
+ * shortest path to m that always takes the lowest-id parent. */
+void orc_relay_tables(int M, const int32_t* adj, int32_t* dist, int32_t* first);
+
+/* quantizer kinds */
+#define ORC_Q_NONE   0
+#define ORC_Q_KMEANS 1
+#define ORC_Q_JPEG   2
+
+/* per-slice statistics written by orc_dadmm_iterate */
+#define ORC_NSTAT 5   /* gap2, change2, norm2_prev, resid2, bytes */
+
+/* One dADMM iteration (Algorithm 4 with Algorithms 2, 3 and Eq. 21-24) for
+ * S independent slices of M nodes each. See oracle.c for the step list.
+ *   sino  [S][A][B]          measured data, natural angle order
+ *   u,lam [S][M][N*N]        local images and duals (updated)
+ *   xseg  [S][N*N]           every owner's unquantized segment (updated)
+ *   hist  [D][3][S][N*N]     dequantized messages, ring of depth
+ *                            D >= max(hop distance) + 1
+ *   iter  in: completed iterations k; out: k+1
+ *   stats [S][ORC_NSTAT]
+ * Returns 0, or a negative code for invalid arguments. */
+int orc_dadmm_iterate(int N, int B, int A, int S, int M,
+                      const double* c, const double* s,
+                      const int32_t* node_ang_ptr, const int32_t* node_ang,
+                      const int32_t* seg_row_ptr,
+                      const int32_t* adj, const int32_t* edge_q,
+                      const int32_t* home_q,
+                      double rho, const double* eta1, double eta2, int E1, int E2,
+                      int km_k, int km_iters, int jpeg_quality, uint64_t seed,
+                      int D, const double* sino, double* u, double* lam,
+                      double* xseg, double* hist, int32_t* iter, double* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

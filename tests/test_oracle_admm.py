@@ -1,0 +1,152 @@
+"""Pins of the oracle's dADMM iteration (Algorithms 2-4, Eq. 15-18, 21-24)
+against consequences of the mathematics: a single node reduces to
+least squares (dense lstsq), exact noise-free data is a fixed point even with
+relay delays, exactly solved sub-problems satisfy the optimality
+conditions of Eq. 15-16 and zero the owner's dual (Eq. 18), the x-update has a closed form, the relay tables
+of a 4-ring are known by hand, and the view every node uses carries exactly
+the hop delay and quantizer the graph dictates."""
+import numpy as np
+import pytest
+
+import oracle as O
+from problems import oracle_eta1, small_problem
+
+
+def dense_P(geo, N, sel=None):
+    return np.stack([geo.project(e.reshape(N, N), sel).ravel() for e in np.eye(N * N)], axis=1)
+
+
+def test_relay_tables_ring4_by_hand():
+    adj = np.zeros((4, 4), np.int32)
+    for m in range(4):
+        adj[m, (m + 1) % 4] = adj[(m + 1) % 4, m] = 1
+    dist, first = O.relay_tables(adj)
+    assert np.array_equal(dist, [[0, 1, 2, 1], [1, 0, 1, 2], [2, 1, 0, 1], [1, 2, 1, 0]])
+    # owner 0 reaches node 2 through its lowest-id parent (1), so via edge (0, 1)
+    assert first[0, 2] == 1 and first[1, 3] == 0 and first[2, 0] == 1 and first[3, 1] == 0
+    assert all(first[s, m] == m for s in range(4) for m in range(4) if dist[s, m] == 1)
+
+
+def test_single_node_converges_to_min_norm_least_squares():
+    """M = 1 and an exact x-step (E2 = 200): lambda vanishes after one
+    iteration and the u-update is proximal-point GD on Eq. 5 from zero, whose
+    limit is the minimum-norm least-squares solution"""
+    N, B, A = 8, 13, 16
+    p = small_problem(N=N, A=A, B=B, M=1, E1=10, E2=200, noise=0.05, seed=1)
+    st = O.DADMM(p, oracle_eta1(p))
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    P = dense_P(geo, N)
+    x_ls = np.linalg.lstsq(P, p["sino"][0].astype(np.float64).ravel(), rcond=None)[0]
+    for _ in range(3500):
+        st.iterate(p["sino"])
+    x = st.home_view()[0].ravel()
+    assert np.linalg.norm(x - x_ls) <= 1e-7 * np.linalg.norm(x_ls)
+    assert np.abs(st.lam).max() < 1e-12
+
+
+@pytest.mark.parametrize("graph,M,quant", [("ring", 4, "none"), ("complete", 3, "none"),
+                                          ("ring", 4, "kmeans")])
+def test_noise_free_truth_is_a_fixed_point(graph, M, quant):
+    """d = P x_true, u_m = x = x_true, lambda = 0: every update leaves the state
+    unchanged, whatever the relay delays"""
+    N, B, A = 8, 13, 16
+    p = small_problem(N=N, A=A, B=B, M=M, graph=graph, quant=quant, km_k=64)
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    rng = np.random.default_rng(4)
+    # quantized runs: the image takes few values, so K-means reproduces it exactly
+    x_true = rng.integers(0, 4, (N, N)).astype(np.float64) if quant != "none" else rng.random((N, N))
+    sino = geo.project(x_true)[None].astype(np.float64)
+    st = O.DADMM(p, oracle_eta1(p))
+    u = np.broadcast_to(x_true, (1, M, N, N))
+    hist = np.broadcast_to(x_true, (st.D, 3, 1, N, N))
+    st.load_state(u, np.zeros((1, M, N, N)), x_true[None], hist, 7)
+    for _ in range(3):
+        stats = st.iterate(sino)
+    assert np.abs(st.u - x_true).max() < 1e-12
+    assert np.abs(st.lam).max() < 1e-12
+    assert np.abs(st.xseg - x_true).max() < 1e-12
+    assert stats[0, 0] < 1e-24 and stats[0, 1] < 1e-24
+
+
+def test_exact_subproblem_solutions_satisfy_their_optimality_conditions():
+    """With E1 and E2 large the GD loops solve Eq. 15 and 16 exactly:
+    P_m^T (P_m u_m - d_m) + rho (u_m - x_m^k) + lambda_m^k = 0 at the new u_m,
+    and x[m] = u_m + lambda_m^k / rho on segment m, which makes the dual
+    update (Eq. 18) return lambda_m = 0 on the node's own segment."""
+    N, B, A, M, rho = 8, 13, 16, 3, 2.0
+    p = small_problem(N=N, A=A, B=B, M=M, graph="complete", E1=3000, E2=80, noise=0.05,
+                      seed=3, rho=rho, eta2=0.5 / rho)
+    st = O.DADMM(p, oracle_eta1(p))
+    rng = np.random.default_rng(2)
+    lam0 = rng.standard_normal((1, M, N, N))
+    hist = np.broadcast_to(rng.random((N, N)), (st.D, 3, 1, N, N))
+    st.load_state(rng.random((1, M, N, N)), lam0, rng.random((1, N, N)), hist, 4)
+    x_k = hist[0, 0, 0]  # complete graph, unquantized: every view of x^k is this image
+    st.iterate(p["sino"])
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    for m in range(M):
+        sel = idx[ptr[m]:ptr[m + 1]]
+        um = st.u[0, m]
+        grad = (geo.backproject(geo.project(um, sel) - p["sino"][0][sel].astype(np.float64), sel)
+                + rho * (um - x_k) + lam0[0, m])
+        assert np.abs(grad).max() < 1e-9 * np.abs(lam0).max()
+        r0, r1 = p["seg_row_ptr"][m], p["seg_row_ptr"][m + 1]
+        assert np.abs(st.xseg[0, r0:r1] - (um + lam0[0, m] / rho)[r0:r1]).max() < 1e-12
+        assert np.abs(st.lam[0, m, r0:r1]).max() < 1e-12
+
+
+def test_x_update_closed_form():
+    """E2 GD steps of Algorithm 3 from x0: v + (1 - eta2 rho)^E2 (x0 - v), v = u + lambda/rho"""
+    N, M = 8, 2
+    p = small_problem(N=N, M=M, E1=0, E2=7, rho=0.7, eta2=0.3)
+    st = O.DADMM(p, np.ones(M))
+    rng = np.random.default_rng(6)
+    u, lam, x0 = rng.random((1, M, N, N)), rng.standard_normal((1, M, N, N)), rng.random((1, N, N))
+    st.load_state(u, lam, x0, np.zeros((st.D, 3, 1, N, N)), 0)
+    st.iterate(np.zeros((1, p["geometry"]["A"], p["geometry"]["B"]), np.float32))
+    f = (1 - 0.3 * 0.7) ** 7
+    for m in range(M):
+        r0, r1 = p["seg_row_ptr"][m], p["seg_row_ptr"][m + 1]
+        v = u[0, m, r0:r1] + lam[0, m, r0:r1] / 0.7
+        assert np.allclose(st.xseg[0, r0:r1], v + f * (x0[0, r0:r1] - v), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("quant", ["none", "alternate"])
+def test_views_follow_hop_delays_and_first_edge_quantizer(quant):
+    """E1 = E2 = 0 and u = 0 turn the dual update into lambda_m = -rho x_m^{k+1},
+    exposing every node's view: segment s reaches node m after
+    max(dist - 1, 0) extra iterations through the plane of its first edge"""
+    N, M, rho = 8, 4, 2.0
+    p = small_problem(N=N, M=M, graph="ring", quant=quant, E1=0, E2=0, rho=rho)
+    st = O.DADMM(p, np.ones(M))
+    D, k = st.D, 5
+    hist = np.zeros((D, 3, 1, N, N))
+    seg = p["seg_row_ptr"]
+    for j in range(D):
+        for q in range(3):
+            for s in range(M):
+                hist[j, q, 0, seg[s]:seg[s + 1]] = 1000 * q + 100 * j + s
+    xseg = np.zeros((1, N, N))
+    for s in range(M):
+        xseg[0, seg[s]:seg[s + 1]] = 7.0 + s  # constant segments: every quantizer is exact
+    st.load_state(np.zeros((1, M, N, N)), np.zeros((1, M, N, N)), xseg, hist, k)
+    st.iterate(np.zeros((1, 16, 13), np.float32))
+    dist, first = O.relay_tables(p["adj"])
+    for m in range(M):
+        view = -st.lam[0, m] / rho
+        for s in range(M):
+            lag = 0 if s == m else dist[s, m] - 1
+            kind = p["home_q"][m] if s == m else p["edge_q"][s, first[s, m]]
+            want = 7.0 + s if lag == 0 else 1000 * kind + 100 * ((k + 1 - lag) % D) + s
+            assert np.all(view[seg[s]:seg[s + 1]] == want), (m, s)
+
+
+def test_bytes_follow_the_communication_model():
+    """complete graph, no quantization: every owner sends its n/M segment to
+    the M - 1 others, M (M-1) n / M values in total (Eq. 20 summed over nodes)"""
+    N, M = 8, 4
+    p = small_problem(N=N, M=M, graph="complete")
+    st = O.DADMM(p, oracle_eta1(p))
+    stats = st.iterate(p["sino"])
+    assert stats[0, 4] == 4.0 * M * (M - 1) * (N * N // M)
