@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the decentralized-ADMM hot path on GB300.
+
+Metric: projector+backprojector GUPS (pixel-angle updates of both operators
+per second, 1e9) and ADMM iterations/s, batched (persistent kernels, one
+CUDA graph per iteration) vs plain (one launch per node and phase), on
+synthetic random-ellipse data shaped like the stress problem: 8 slices of
+2048 x 2048, 1800 angles, 2897 bins, 64 nodes per slice with uneven angle
+counts (8..60) on a random geometric graph of mean degree 6, K-means (k=32)
+and JPEG (quality 75) messages alternated per edge, E1 = E2 = 10.
+
+A step is one ADMM iteration over all slices and nodes. Inputs (u, lambda,
+history: ~20 GB) are far larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this build has no GPU implementation).
+Under torchrun every rank runs its own replica (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "projector+backprojector GUPS and ADMM iter/s, batched vs plain on 1 GB300 at rel-L2 ≤1e-3"
+UNIT = "GUPS"
+FLOP_PER_UPDATE = 8.0  # 2 touched bins x (ramp FMA + weight x value FMA)
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c5_stress")
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-nodes", type=int, default=2, help="oracle sample: nodes of slice 0")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# process group (one process per GPU)
+# ---------------------------------------------------------------------------
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    """maximum of a float over all ranks (the slowest rank sets the job time)"""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws):
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons every 200 ms during the timed region"""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def updates_per_iteration(prob):
+    g = prob["geometry"]
+    return 2.0 * prob["E1"] * prob["S"] * g["A"] * g["N"] * g["N"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel):
+    """ncu DRAM bytes per launch from the committed summary, if it was taken on
+    the current kernel source (else None)"""
+    src = os.path.join(ROOT, "paper_2410_06106_gb300", "csrc", "operators.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get(kernel)
+    if not e or e.get("source_sha256_16") != digest:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_sample(prob, nodes):
+    """FP64 oracle, one Algorithm 2 inner step (P_m u, residual, P_m^T r,
+    update) for the first `nodes` nodes of slice 0; returns (updates, seconds)"""
+    import oracle as O
+    g = prob["geometry"]
+    N, B = g["N"], g["B"]
+    geo = O.Geometry(N, B, g["theta"])
+    rng = np.random.default_rng(5)
+    u = rng.random((N, N))
+    ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
+    upd = 0.0
+    t0 = time.perf_counter()
+    for m in range(nodes):
+        sel = idx[ptr[m]:ptr[m + 1]]
+        r = geo.project(u, sel) - prob["sino"][0][sel]
+        gr = geo.backproject(r, sel)
+        u = u - 1e-6 * (gr + 1.0 * u)
+        upd += 2.0 * len(sel) * N * N
+    return upd, time.perf_counter() - t0
+
+
+def run_reference(args, ws, rank):
+    """reference arm: the FP64 CPU oracle as it stands, rank 0 only"""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2410_06106_gb300 import synth
+    prob = synth.make_problem(args.workload, slices=1)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(prob, 1)
+    tot_u, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        u, t = cpu_oracle_sample(prob, 1)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t / 1e9
+    cores = O.num_threads()
+    sample = ("one Algorithm 2 inner step (projection, residual, backprojection, update) of node 0 of "
+              "slice 0 per step, FP64 oracle, %d OpenMP threads" % cores)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.workload),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name):
+    from paper_2410_06106_gb300 import synth
+    c = synth.CONFIGS[name]
+    return {"workload": name, "N": c["N"], "angles": c["A"], "bins": c["B"], "nodes": c["M"],
+            "slices": c["S"], "graph": "%s" % (c["graph"],), "partition": "%s" % (c["part"],),
+            "quantizer": c["quant"], "E1": 10, "E2": 10, "l2": "inputs larger than L2 (no flush)"}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2410_06106_gb300 import api, synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob = synth.make_problem(args.workload)
+    g = prob["geometry"]
+    geo = api.Geometry(g["N"], g["B"], g["theta"])
+    ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
+    L = np.array([geo.opnorm_sq(idx[ptr[m]:ptr[m + 1]], iters=20) for m in range(prob["M"])])
+    eta1 = 1.0 / (L + prob["rho"])
+    sino_host = torch.as_tensor(prob["sino"]).pin_memory()
+    sino = sino_host.to(dev)
+    upd = updates_per_iteration(prob)
+    stream = torch.cuda.Stream(dev)
+
+    with torch.cuda.stream(stream):
+        s = api.DADMM(prob, eta1, mode="batched", geometry=geo)
+        s.set_profiling(True)
+        for _ in range(args.warmup):
+            s.step(sino, 1, stats=False)
+        torch.cuda.synchronize()
+        names = s.phase_names()
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        phase_ms = np.zeros(len(names))
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.step(sino, 1, stats=False)
+            phase_ms += s.phase_times()  # events inside the captured graph
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        stats = s.step(sino, 1, stats=True)  # untimed: statistics of one more iteration
+        s.set_profiling(False)
+        del s
+
+    ms_max = max_over_ranks(ms, ws)
+    total_upd = sum_over_ranks(upd, ws)
+    value = total_upd / (ms_max * 1e-3) / 1e9
+
+    # dominant kernel from the live phase timing
+    E1 = prob["E1"]
+    bp_ms = phase_ms[[2 * e + 1 for e in range(E1)]].sum() / (args.steps * E1)
+    pj_ms = phase_ms[[2 * e for e in range(E1)]].sum() / (args.steps * E1)
+    upd_per_launch = upd / (2.0 * E1)
+    dominant = "backproject_ustep" if bp_ms >= pj_ms else "project"
+    dom_ms = max(bp_ms, pj_ms)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2.0 * sm_max * 1e6 / 1e12
+    achieved = FLOP_PER_UPDATE * upd_per_launch / (dom_ms * 1e-3) / 1e12
+    traffic = profile_traffic(dominant)
+
+    plain = None
+    if not args.no_plain:
+        with torch.cuda.stream(stream):
+            p = api.DADMM(prob, eta1, mode="plain", geometry=geo)
+            p.step(sino, 1, stats=False)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.plain_steps):
+                p.step(sino, 1, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms = e0.elapsed_time(e1) / args.plain_steps
+            del p
+        pms = max_over_ranks(pms, ws)
+        plain = {"value": total_upd / (pms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pms,
+                 "iters_per_s": 1e3 / pms, "steps": args.plain_steps}
+
+    e2e = None
+    if not args.no_e2e:
+        with torch.cuda.stream(stream):
+            s = api.DADMM(prob, eta1, mode="batched", geometry=geo)
+            out_host = torch.empty(prob["S"], g["N"], g["N"], pin_memory=True)
+            s.step(sino, 1, stats=False)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                d = sino_host.to(dev, non_blocking=True)  # this step's input, H2D from pinned memory
+                s.step(d, 1, stats=False)
+                out_host.copy_(s.home_view(), non_blocking=True)  # D2H of the step's result
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ems = e0.elapsed_time(e1) / args.steps
+            del s
+        ems = max_over_ranks(ems, ws)
+        e2e = {"value": total_upd / (ems * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ems,
+               "h2d_bytes_per_step": int(sino_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle as O
+        cu, ct = cpu_oracle_sample(prob, args.cpu_nodes)
+        cpu = {"value": cu / ct / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+               "sample": "one Algorithm 2 inner step of nodes 0..%d of slice 0 (%.3g updates, %.1f s)"
+                         % (args.cpu_nodes - 1, cu, ct)}
+
+    launches_per_iter = 2 * E1 + 6
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "iters_per_s": 1e3 / ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded random-ellipse phantoms, analytic sinograms, 1% noise)",
+                "config": dict(workload_config(args.workload), parallelism="replicas" if ws > 1 else "single",
+                               mode="batched persistent, graph-captured"),
+                "plain": plain, "e2e": e2e,
+                "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_tflops,
+                             "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                             "ms_per_launch": dom_ms, "updates_per_launch": upd_per_launch,
+                             "flop_per_update": FLOP_PER_UPDATE,
+                             "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock of "
+                                           "MEASURED_PEAKS.json)" % (sms, FP32_LANES_PER_SM, sm_max),
+                             "project_ms_per_launch": pj_ms, "backproject_ms_per_launch": bp_ms},
+                "phase_ms_per_step": {n: float(v / args.steps) for n, v in zip(names, phase_ms)},
+                "cpu_baseline": cpu, "clocks": ck,
+                "gpu_launches": launches_per_iter * args.steps,
+                "stats_last_iter": {"gap2": float(stats[0, :, 0].sum()), "bytes": float(stats[0, :, 4].sum())}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,267 @@
+/*
+ * tomo.h - C ABI of the GB300 (sm_103a) library for decentralized ADMM
+ * tomographic reconstruction with quantized messages
+ * ("Distributed Tomographic Reconstruction with Quantization", Miao, Aslan,
+ * Koyuncu, Gursoy, arXiv 2410.06106).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All functions return tomo_status: TOMO_OK (0) or a negative error code.
+ *   tomo_last_error() gives a message for the calling thread's last error.
+ * - Argument errors (null pointers, sizes out of range, a geometry used on a
+ *   different device) are detected on the host BEFORE anything is launched;
+ *   the call then returns TOMO_ERR_INVALID_ARG and has no effect.
+ * - Array arguments are caller-owned DEVICE pointers unless stated otherwise
+ *   (PyTorch or cudaMalloc memory of the current device); the library never
+ *   frees them and keeps no reference after the call returns, except the
+ *   state pointers captured by dadmm_step (see there). Opaque handles are
+ *   library-owned and released by their destroy call.
+ * - Work is enqueued asynchronously on `stream` (NULL = legacy default
+ *   stream); no call synchronizes unless documented.
+ * - Images are float32 [N][N] row-major, pixel (i, j) centred at
+ *   x = j - (N-1)/2, y = (N-1)/2 - i (row 0 at the top, y up), unit pixels.
+ *   Sinograms are float32 [angles][B] row-major; ray (a, b) is the line
+ *   x cos(theta_a) + y sin(theta_a) = t_b, t_b = b - (B-1)/2.
+ * - The system matrix entry P[(a,b),(i,j)] is the length of the
+ *   intersection of ray (a, b) with pixel (i, j) (Sec. 2.1, Eq. 2); a ray
+ *   lying exactly on the edge between two pixels gives each half the length.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TOMO_API __attribute__((visibility("default")))
+#else
+#define TOMO_API
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* tomo_stream_t; /* same type as cudaStream_t */
+
+typedef int tomo_status;
+#define TOMO_OK 0
+#define TOMO_ERR_INVALID_ARG -1 /* bad argument, nothing launched */
+#define TOMO_ERR_CUDA -2        /* a CUDA runtime call failed */
+#define TOMO_ERR_WORKSPACE -3   /* workspace / constant table too small */
+#define TOMO_ERR_TIMEOUT -4     /* reserved: a bounded device wait gave up */
+#define TOMO_ERR_NUMERIC -5     /* non-finite values reached the statistics */
+
+/* Message of the calling thread's most recent error ("" if none). The string
+ * stays valid until the next failing call on the same thread. */
+TOMO_API const char* tomo_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+TOMO_API int tomo_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Geometry and the discrete x-ray transform (Sec. 2.1, Eq. 1-4)      */
+/* ------------------------------------------------------------------ */
+
+typedef struct tomo_geometry* tomo_geometry_t;
+
+/* Create a parallel-beam geometry: N x N unit pixels, n_bins unit detector
+ * bins, n_angles projection angles. angles_rad: HOST array of n_angles
+ * radians, or NULL for theta_a = a pi / n_angles (uniform on [0, pi)).
+ * Angles within 1e-12 rad of a multiple of pi/2 are snapped so that their
+ * cosine and sine are exactly 0 or +-1.
+ * The per-angle trig table is copied into the current device's constant
+ * memory (a pool of TOMO_MAX_CONST_ANGLES angles shared by all live
+ * geometries of the process); TOMO_ERR_WORKSPACE if the pool is full.
+ * Limits: 1 <= N <= 8192, 1 <= n_bins <= 16384, 1 <= n_angles <= 4096. */
+#define TOMO_MAX_CONST_ANGLES 3584
+TOMO_API tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* angles_rad,
+                                 tomo_geometry_t* out);
+TOMO_API tomo_status tomo_geometry_destroy(tomo_geometry_t g);
+
+/* Forward projection, Eq. 4 restricted to a subset of angles:
+ *   sino[k][q][b] = sum_{i,j} P[(angle_idx[q], b), (i,j)] img[k][i][j]
+ *                   - (subtract ? subtract[k][q][b] : 0)
+ * img      [batch][N][N]      device, read
+ * sino     [batch][n_sel][B]  device, written (every element)
+ * angle_idx[n_sel]            HOST int32 angle indices (NULL = all angles,
+ *                             then n_sel must equal n_angles); read during
+ *                             the call only
+ * subtract [batch][n_sel][B]  device or NULL (the data term d of Alg. 2)
+ * Ray-driven kernel, FP32 arithmetic, FP32 accumulation. */
+TOMO_API tomo_status tomo_project(tomo_geometry_t g, const float* img, float* sino,
+                         const int32_t* angle_idx, int n_sel, int batch,
+                         const float* subtract, tomo_stream_t stream);
+
+/* Matched backprojection (the exact transpose of tomo_project's matrix):
+ *   img[k][i][j] = beta * img[k][i][j] + sum_{q,b} P[(angle_idx[q], b),(i,j)] sino[k][q][b]
+ * beta must be 0 or 1 (0: img is not read). Same layouts and ownership as
+ * tomo_project. Pixel-driven kernel, FP32. */
+TOMO_API tomo_status tomo_backproject(tomo_geometry_t g, const float* sino, float* img,
+                             const int32_t* angle_idx, int n_sel, int batch, float beta,
+                             tomo_stream_t stream);
+
+/* Squared spectral norm ||P_sel||_2^2 by `iters` power iterations on
+ * P_sel^T P_sel from a seeded start vector. work: device scratch of at least
+ * tomo_opnorm_workspace_size() bytes. Synchronizes the stream; result in
+ * *out (host). Used to choose the Algorithm 2 step eta1 = 1/(L + rho). */
+TOMO_API size_t tomo_opnorm_workspace_size(tomo_geometry_t g, int n_sel);
+TOMO_API tomo_status tomo_opnorm_sq(tomo_geometry_t g, const int32_t* angle_idx, int n_sel, int iters,
+                           uint64_t seed, void* work, size_t work_bytes, double* out,
+                           tomo_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Message quantizers (Sec. 2.7)                                       */
+/* ------------------------------------------------------------------ */
+
+/* Scalar K-means quantizer of one vector (Algorithm 5, Eq. 23).
+ * in [n] device float32; codes [n] uint8 (centre index); centroids [k]
+ * float32; deq [n] float32 = centroids[codes]; objective [iters+1] float64
+ * or NULL (distortion after each assignment step).
+ * Initial centres: the values at k indices drawn by the splitmix64 counter
+ * key `key` (an index whose value is already a centre moves to the next
+ * index, at most 64 times), sorted ascending. Then `iters` Lloyd
+ * iterations: assign every value to the nearest centre by FP32 distance
+ * (ties to the lower index); move each centre to the mean of its members
+ * (FP64 sums, warp-shuffle reductions); empty clusters keep their centre.
+ * A final assignment produces codes and deq. 1 <= k <= 32, n >= 1. */
+TOMO_API tomo_status quant_kmeans(const float* in, int64_t n, int k, int iters, uint64_t key,
+                         uint8_t* codes, float* centroids, float* deq, double* objective,
+                         tomo_stream_t stream);
+
+/* Counter key of the K-means initialisation for (seed, slice, owner,
+ * iteration), as used by dadmm_step. Host function. */
+TOMO_API uint64_t quant_kmeans_key(uint64_t seed, int slice, int owner, int iteration);
+
+/* JPEG-style quantizer of one rows x cols segment (Sec. 2.7 "standard
+ * JPEG"; rows, cols multiples of 8). Per segment lo = min, hi = max; FP32
+ * sample map s = round(255 (v - lo) / (hi - lo)) - 128; orthonormal 8x8
+ * DCT-II in registers; q = round(F / Qt) with the ITU-T T.81 Annex K
+ * luminance table scaled to `quality` (IJG rule); dequantize, inverse DCT,
+ * +128, round, clamp to [0, 255]; v' = lo + s'' (hi - lo) / 255 (hi for
+ * s'' = 255). Rounding is half away from zero. A constant segment is sent
+ * exactly (all coefficients 0). in, deq [rows][cols] float32; coefs
+ * [rows/8][cols/8][64] int16 natural order (may be NULL); lohi [2] float32
+ * (may be NULL); nnz: device int64 counter INCREMENTED by the number of
+ * non-zero coefficients (may be NULL). 1 <= quality <= 100. */
+TOMO_API tomo_status quant_jpeg(const float* in, int rows, int cols, int quality, int16_t* coefs,
+                       float* lohi, float* deq, int64_t* nnz, tomo_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Decentralized ADMM with quantized messages (Sec. 2.4-2.7, Alg. 2-4)  */
+/* ------------------------------------------------------------------ */
+
+#define DADMM_Q_NONE 0
+#define DADMM_Q_KMEANS 1
+#define DADMM_Q_JPEG 2
+
+#define DADMM_MODE_BATCHED 0 /* one persistent launch per phase, CUDA graph */
+#define DADMM_MODE_PLAIN 1   /* one launch per node and phase, no graph */
+
+/* Problem description (all pointers are HOST arrays, copied by dadmm_create).
+ * S independent slices share the geometry, the node split and the graph.
+ *   node_ang_ptr [M+1], node_ang [n_angles]: CSR list of the angles each node
+ *     holds (every angle belongs to exactly one node);
+ *   seg_row_ptr [M+1]: segment m of x is the row band
+ *     [seg_row_ptr[m], seg_row_ptr[m+1]); 0 = seg_row_ptr[0] < ... = N;
+ *   adj [M*M]: symmetric 0/1 adjacency of the message graph (connected);
+ *   edge_q [M*M]: quantizer kind of each edge (ignored where adj = 0);
+ *   home_q [M]: quantizer of each node's own copy of its segment;
+ *   eta1 [M]: Algorithm 2 step per node; eta2: Algorithm 3 step;
+ *   E1, E2: inner GD steps; rho: penalty (Eq. 7);
+ *   km_k, km_iters: K-means centres (<= 32) and Lloyd iterations;
+ *   jpeg_quality: 1..100 (JPEG segments need rows and N multiples of 8);
+ *   seed: K-means initialisation seed; mode: DADMM_MODE_*. */
+typedef struct {
+    int N, n_bins, n_angles, S, M;
+    const int32_t* node_ang_ptr;
+    const int32_t* node_ang;
+    const int32_t* seg_row_ptr;
+    const int32_t* adj;
+    const int32_t* edge_q;
+    const int32_t* home_q;
+    const double* eta1;
+    double eta2, rho;
+    int E1, E2;
+    int km_k, km_iters, jpeg_quality;
+    uint64_t seed;
+    int mode;
+} dadmm_config;
+
+typedef struct dadmm* dadmm_t;
+
+/* Create a solver for geometry g (which must outlive it). Builds the relay
+ * tables (hop distance and first edge of the lowest-id shortest path from
+ * every owner to every node), the persistent-kernel work lists and the
+ * autotuned launch shapes. Allocates only small device tables owned by the
+ * handle. */
+TOMO_API tomo_status dadmm_create(tomo_geometry_t g, const dadmm_config* cfg, dadmm_t* out);
+TOMO_API tomo_status dadmm_destroy(dadmm_t h);
+
+/* Depth D of the message ring (maximum hop distance + 1). */
+TOMO_API int dadmm_ring_depth(dadmm_t h);
+
+/* Device state, all caller-owned float32 unless noted:
+ *   u, lam  [S][M][N][N]    local images u_m and duals lambda_m
+ *   xseg    [S][N][N]       every owner's unquantized segment x[m]
+ *   hist    [D][3][S][N][N] dequantized messages by (iteration mod D, kind)
+ *   iter    int32 [1]       completed iterations k
+ * dadmm_state_init zeroes all of it (Algorithm 4 starts from zero). */
+typedef struct {
+    float* u;
+    float* lam;
+    float* xseg;
+    float* hist;
+    int32_t* iter;
+} dadmm_state;
+
+TOMO_API size_t dadmm_state_size(dadmm_t h); /* bytes of u+lam+xseg+hist+iter, for sizing */
+TOMO_API tomo_status dadmm_state_init(dadmm_t h, const dadmm_state* st, tomo_stream_t stream);
+
+/* Scratch for dadmm_step (residuals, codec scratch, partial sums); device,
+ * caller-owned, at least dadmm_workspace_size() bytes, 256-byte aligned. */
+TOMO_API size_t dadmm_workspace_size(dadmm_t h);
+
+/* Per-iteration, per-slice statistics (float64), in this order:
+ *   0 gap2   sum_m ||u_m - x_m^{k+1}||^2 (primal residual)
+ *   1 chg2   ||x_0^{k+1} - x_0^k||^2 (node 0's view)
+ *   2 nrm2   ||x_0^k||^2 (stopping test chg2 / nrm2 < 1e-12, i.e. 1e-6 rel.)
+ *   3 res2   sum_m ||P_m u_m - d_m||^2 at the last inner step
+ *   4 bytes  message bytes sent over the graph in this iteration */
+#define DADMM_NSTAT 5
+
+/* Run n_iters iterations of Algorithm 4 on sinograms sino [S][n_angles][B]
+ * (device, natural angle order). Each iteration: E1 x {projector + residual,
+ * matched backprojector + fused u step} for every node and slice; E2 segment
+ * steps + K-means / JPEG messages for every owner; assembly of every node's
+ * view through the message ring + dual update + FP64 norms.
+ * BATCHED mode captures one iteration as a CUDA graph (re-captured when the
+ * state/workspace/sino pointers or the stream change) and replays it.
+ * stats: HOST [n_iters][S][DADMM_NSTAT] or NULL; when non-NULL the call
+ * synchronizes the stream and fills it. Returns TOMO_ERR_NUMERIC if a
+ * statistic is not finite (the state is still advanced). */
+TOMO_API tomo_status dadmm_step(dadmm_t h, const dadmm_state* st, const float* sino, int n_iters,
+                       void* workspace, size_t workspace_bytes, double* stats,
+                       tomo_stream_t stream);
+
+/* Per-phase timing of the iterations. When enabled, dadmm_step records a
+ * CUDA event (timing enabled) before and after every phase launch of an
+ * iteration, inside the captured graph in BATCHED mode; phases are, in
+ * order: E1 x (projector, backprojector + u-step), x-step, K-means, JPEG,
+ * dual update + norms, statistics. Enabling or disabling forces a new
+ * capture. dadmm_phase_times synchronizes on the most recent iteration's
+ * last event and writes min(n, dadmm_num_phases()) durations in ms. */
+TOMO_API tomo_status dadmm_set_profiling(dadmm_t h, int enable);
+TOMO_API int dadmm_num_phases(dadmm_t h);
+TOMO_API tomo_status dadmm_phase_times(dadmm_t h, float* ms, int n);
+
+/* x as reconstructed by the owners: rows of segment m taken from the
+ * home-quantized message of owner m at the current iteration (zero before
+ * the first iteration). out [S][N][N] device. */
+TOMO_API tomo_status dadmm_home_view(dadmm_t h, const dadmm_state* st, float* out, tomo_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOMO_H */

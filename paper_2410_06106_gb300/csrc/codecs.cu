@@ -1,0 +1,514 @@
+// Message quantizers of dADMM-K and dADMM-J (Sec. 2.7) on GB300:
+//   - scalar K-means (Algorithm 5): one CTA per vector, warp-parallel seeded
+//     initialisation, FP32 nearest-centre decisions, FP64 centroid sums kept
+//     per thread in shared memory and combined with warp shuffles in a fixed
+//     order (deterministic);
+//   - JPEG-style codec: one thread per 8x8 block, the orthonormal DCT-II and
+//     its inverse separable in registers on the FP32 cores, luminance table
+//     of ITU-T T.81 Annex K scaled by the IJG quality rule.
+// Both have a standalone entry (quant_kmeans / quant_jpeg) and a dADMM form
+// that takes every owner segment of an iteration in one launch.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
+
+// ------------------------------------------------------------------
+// K-means
+// ------------------------------------------------------------------
+size_t kmeans_smem(int kmax) {
+    return (size_t)kmax * kKmThreads * (sizeof(double) + sizeof(int)) + kmax * sizeof(float) +
+           32 * sizeof(double);
+}
+
+template <int KMAX>
+__device__ void kmeans_block(const float* __restrict__ in, long long n, int k, int iters, uint64_t key,
+                             uint8_t* codes, float* cent_out, float* deq, double* obj) {
+    extern __shared__ __align__(16) unsigned char km_smem[];
+    double* s_sum = reinterpret_cast<double*>(km_smem);               // [KMAX][256]
+    int* s_cnt = reinterpret_cast<int*>(s_sum + KMAX * kKmThreads);    // [KMAX][256]
+    float* s_cent = reinterpret_cast<float*>(s_cnt + KMAX * kKmThreads);
+    // 32 doubles after the centres: byte offset KMAX * (256 * 12 + 4), a multiple of 8
+    double* s_red = reinterpret_cast<double*>(km_smem + (size_t)KMAX * (kKmThreads * 12 + 4));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned full = 0xffffffffu;
+    const uint64_t un = (uint64_t)n;
+
+    // initial centres: value at a seeded index, moving to the next index while
+    // the value is already a centre (64 probes at most, checked 32 at a time)
+    if (warp == 0) {
+        for (int j = 0; j < k; ++j) {
+            const uint64_t idx = mix64(key + (uint64_t)(j + 1) * kGolden) % un;
+            float pick = in[idx];
+            for (int round = 0; round < kKmProbes / 32; ++round) {
+                const float cand = in[(idx + (uint64_t)(round * 32 + lane)) % un];
+                bool dup = false;
+                for (int q = 0; q < j; ++q) dup |= (s_cent[q] == cand);
+                const unsigned bal = __ballot_sync(full, !dup);
+                if (bal) {
+                    pick = __shfl_sync(full, cand, __ffs(bal) - 1);
+                    break;
+                }
+            }
+            if (lane == 0) s_cent[j] = pick;
+            __syncwarp();
+        }
+        if (lane == 0)
+            for (int j = 1; j < k; ++j) {  // ascending order
+                const float t = s_cent[j];
+                int q = j - 1;
+                while (q >= 0 && s_cent[q] > t) {
+                    s_cent[q + 1] = s_cent[q];
+                    --q;
+                }
+                s_cent[q + 1] = t;
+            }
+    }
+    __syncthreads();
+
+    for (int t = 0; t <= iters; ++t) {
+        const bool last = (t == iters);
+        float cr[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) cr[j] = j < k ? s_cent[j] : INFINITY;
+        if (!last)
+            for (int j = 0; j < k; ++j) {
+                s_sum[j * kKmThreads + tid] = 0.0;
+                s_cnt[j * kKmThreads + tid] = 0;
+            }
+        double J = 0.0;
+        for (long long i = tid; i < n; i += kKmThreads) {
+            const float v = in[i];
+            int best = 0;
+            float bd = fabsf(v - cr[0]);
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j) {
+                const float d = fabsf(v - cr[j]);
+                if (d < bd) {  // strict: ties stay with the lower index
+                    bd = d;
+                    best = j;
+                }
+            }
+            if (last) {
+                if (codes) codes[i] = (uint8_t)best;
+                deq[i] = s_cent[best];
+            } else {
+                s_sum[best * kKmThreads + tid] += (double)v;
+                s_cnt[best * kKmThreads + tid] += 1;
+            }
+            if (obj) {
+                const double e = (double)v - (double)s_cent[best];
+                J += e * e;
+            }
+        }
+        if (obj) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) J += __shfl_xor_sync(full, J, o);
+            if (lane == 0) s_red[warp] = J;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < kKmThreads / 32; ++w) tot += s_red[w];
+                obj[t] = tot;
+            }
+        }
+        if (last) break;
+        __syncthreads();
+        // centre update: member sums in a fixed order (8 per lane, then a shuffle tree)
+        for (int j = warp; j < k; j += kKmThreads / 32) {
+            double sm = 0.0;
+            int c = 0;
+#pragma unroll
+            for (int r = 0; r < kKmThreads / 32; ++r) {
+                sm += s_sum[j * kKmThreads + lane + 32 * r];
+                c += s_cnt[j * kKmThreads + lane + 32 * r];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sm += __shfl_xor_sync(full, sm, o);
+                c += __shfl_xor_sync(full, c, o);
+            }
+            if (lane == 0 && c > 0) s_cent[j] = (float)(sm / (double)c);
+        }
+        __syncthreads();
+    }
+    if (cent_out && tid < k) cent_out[tid] = s_cent[tid];
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kKmThreads) kmeans_single_kernel(const float* in, long long n, int k,
+                                                                   int iters, uint64_t key, uint8_t* codes,
+                                                                   float* cent, float* deq, double* obj) {
+    kmeans_block<KMAX>(in, n, k, iters, key, codes, cent, deq, obj);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kKmThreads) kmeans_dadmm_kernel(const DadmmCodec p, int k, int iters,
+                                                                  int task_begin) {
+    const SegTask T = p.tasks[task_begin + blockIdx.x];
+    const int kk = *p.iter;  // completed iterations: the messages are x^{k+1}
+    const size_t n = (size_t)p.N * p.N;
+    const size_t off = (size_t)T.slice * n + (size_t)T.r0 * p.N;
+    const long long len = (long long)(T.r1 - T.r0) * p.N;
+    const int slot = (kk + 1) % p.D;
+    float* deq = p.hist + ((size_t)slot * 3 + DADMM_Q_KMEANS) * p.S * n + off;
+    kmeans_block<KMAX>(p.xseg + off, len, k, iters, kmeans_key(p.seed, T.slice, T.owner, kk + 1),
+                       nullptr, nullptr, deq, nullptr);
+}
+
+template <class F>
+static void with_kmax(int k, F&& f) {
+    if (k <= 8)
+        f(std::integral_constant<int, 8>());
+    else if (k <= 16)
+        f(std::integral_constant<int, 16>());
+    else
+        f(std::integral_constant<int, 32>());
+}
+
+void launch_kmeans_single(const float* in, long long n, int k, int iters, uint64_t key, uint8_t* codes,
+                          float* cent, float* deq, double* obj, cudaStream_t st) {
+    with_kmax(k, [&](auto KM) {
+        constexpr int KMAX = decltype(KM)::value;
+        const size_t sm = kmeans_smem(KMAX);
+        static bool attr = false;  // set once, before any stream capture
+        if (!attr) {
+            TOMO_CUDA(cudaFuncSetAttribute(kmeans_single_kernel<KMAX>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            attr = true;
+        }
+        kmeans_single_kernel<KMAX><<<1, kKmThreads, sm, st>>>(in, n, k, iters, key, codes, cent, deq, obj);
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
+
+void launch_kmeans_dadmm(const DadmmCodec& p, int k, int iters, int task_begin, int task_count,
+                         cudaStream_t st) {
+    if (task_count <= 0) return;
+    with_kmax(k, [&](auto KM) {
+        constexpr int KMAX = decltype(KM)::value;
+        const size_t sm = kmeans_smem(KMAX);
+        static bool attr = false;  // set once, before any stream capture
+        if (!attr) {
+            TOMO_CUDA(cudaFuncSetAttribute(kmeans_dadmm_kernel<KMAX>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            attr = true;
+        }
+        kmeans_dadmm_kernel<KMAX><<<task_count, kKmThreads, sm, st>>>(p, k, iters, task_begin);
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
+
+// ------------------------------------------------------------------
+// JPEG
+// ------------------------------------------------------------------
+
+// ITU-T T.81 (1992) Annex K, Table K.1, luminance, natural order
+static const int kJpegLuma[64] = {16, 11, 10, 16, 24,  40,  51,  61,  12, 12, 14, 19, 26,  58,  60,  55,
+                                  14, 13, 16, 24, 40,  57,  69,  56,  14, 17, 22, 29, 51,  87,  80,  62,
+                                  18, 22, 37, 56, 68,  109, 103, 77,  24, 35, 55, 64, 81,  104, 113, 92,
+                                  49, 64, 78, 87, 103, 121, 120, 101, 72, 92, 95, 98, 112, 100, 103, 99};
+
+void jpeg_quant_table(int quality, int32_t* qt) {
+    quality = quality < 1 ? 1 : quality > 100 ? 100 : quality;
+    const int scale = quality < 50 ? 5000 / quality : 200 - 2 * quality;  // IJG rule
+    for (int i = 0; i < 64; ++i) {
+        const long v = ((long)kJpegLuma[i] * scale + 50) / 100;
+        qt[i] = (int32_t)(v < 1 ? 1 : v > 255 ? 255 : v);
+    }
+}
+
+// basis[p][x] = C(p)/2 cos((2x+1) p pi / 16), C(0) = 1/sqrt(2)
+__constant__ float c_dct[64];
+
+static void ensure_dct_table() {
+    static std::mutex mu;
+    static std::vector<char> done;
+    int dev = 0;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (done[dev]) return;
+    float h[64];
+    for (int p = 0; p < 8; ++p)
+        for (int x = 0; x < 8; ++x)
+            h[p * 8 + x] = (float)((p == 0 ? 1.0 / std::sqrt(2.0) : 1.0) * 0.5 *
+                                   std::cos((2 * x + 1) * p * 3.14159265358979323846 / 16.0));
+    TOMO_CUDA(cudaMemcpyToSymbol(c_dct, h, sizeof(h)));
+    done[dev] = 1;
+}
+
+struct QTable {
+    int q[64];
+};
+
+// one 8x8 block: src/dst point at its top-left value, `stride` floats per row.
+// Returns the number of non-zero quantized coefficients.
+__device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* __restrict__ dst, int stride,
+                                          float lo, float hi, const QTable& qt, int16_t* coefs) {
+    const float rng = __fsub_rn(hi, lo);
+    const float inv = __fdiv_rn(255.0f, rng);
+    const float step = __fdiv_rn(rng, 255.0f);
+    float b[64];
+    float dcs = 0.f;  // sum of the integer samples: exact in FP32
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 v0 = *reinterpret_cast<const float4*>(src + (size_t)i * stride);
+        const float4 v1 = *reinterpret_cast<const float4*>(src + (size_t)i * stride + 4);
+        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float t = __fmul_rn(__fsub_rn(v[j], lo), inv);
+            const float r = fminf(fmaxf(roundf(t), 0.0f), 255.0f);  // round half away from zero
+            b[i * 8 + j] = r - 128.0f;
+            dcs += b[i * 8 + j];
+        }
+    }
+    // forward DCT: rows, then columns
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = b[i * 8 + j];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float a = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a = fmaf(t[j], c_dct[q * 8 + j], a);
+            b[i * 8 + q] = a;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = b[i * 8 + q];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            float a = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a = fmaf(c_dct[p * 8 + i], t[i], a);
+            b[p * 8 + q] = a;
+        }
+    }
+    b[0] = dcs * 0.125f;  // exact DC term: ties of F00 / Qt are decided exactly
+    int nnz = 0;
+#pragma unroll
+    for (int e = 0; e < 64; ++e) {
+        float qv = roundf(__fdiv_rn(b[e], (float)qt.q[e]));
+        qv = fminf(fmaxf(qv, -32768.0f), 32767.0f);
+        if (coefs) coefs[e] = (int16_t)qv;
+        nnz += (qv != 0.0f);
+        b[e] = qv * (float)qt.q[e];  // integer product: exact
+    }
+    const float dcv = b[0] * 0.125f + 128.0f;  // exact DC contribution + level shift
+    b[0] = 0.f;
+    // inverse DCT of the AC part: columns, then rows
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float t[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) t[p] = b[p * 8 + q];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) a = fmaf(c_dct[p * 8 + i], t[p], a);
+            b[i * 8 + q] = a;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = b[i * 8 + q];
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a = fmaf(t[q], c_dct[q * 8 + j], a);
+            const float r = fminf(fmaxf(roundf(a + dcv), 0.0f), 255.0f);
+            o[j] = (r == 255.0f) ? hi : __fadd_rn(lo, __fmul_rn(r, step));
+        }
+        *reinterpret_cast<float4*>(dst + (size_t)i * stride) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(dst + (size_t)i * stride + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    return nnz;
+}
+
+__device__ __forceinline__ void jpeg_const_block(float* dst, int stride, float lo) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        *reinterpret_cast<float4*>(dst + (size_t)i * stride) = make_float4(lo, lo, lo, lo);
+        *reinterpret_cast<float4*>(dst + (size_t)i * stride + 4) = make_float4(lo, lo, lo, lo);
+    }
+}
+
+// min / max of one segment with one block (standalone path)
+__global__ void minmax_kernel(const float* in, long long n, float* lohi) {
+    __shared__ float s_lo[32], s_hi[32];
+    float lo = INFINITY, hi = -INFINITY;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        lo = fminf(lo, in[i]);
+        hi = fmaxf(hi, in[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fminf(lo, s_lo[w]);
+            hi = fmaxf(hi, s_hi[w]);
+        }
+        lohi[0] = lo;
+        lohi[1] = hi;
+    }
+}
+
+constexpr int kJpegThreads = 64;
+
+__global__ void __launch_bounds__(kJpegThreads) jpeg_single_kernel(const float* in, int rows, int cols,
+                                                                   const QTable qt, int16_t* coefs,
+                                                                   const float* lohi, float* deq,
+                                                                   long long* nnz) {
+    const int bpr = cols / 8;
+    const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
+    int c = 0;
+    if (blk < (rows / 8) * bpr) {
+        const int bi = blk / bpr, bj = blk - bi * bpr;
+        const size_t o = (size_t)bi * 8 * cols + (size_t)bj * 8;
+        const float lo = lohi[0], hi = lohi[1];
+        int16_t* cf = coefs ? coefs + (size_t)blk * 64 : nullptr;
+        if (hi > lo) {
+            c = jpeg_block(in + o, deq + o, cols, lo, hi, qt, cf);
+        } else {
+            jpeg_const_block(deq + o, cols, lo);
+            if (cf)
+                for (int e = 0; e < 64; ++e) cf[e] = 0;
+        }
+    }
+    if (nnz) {
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)nnz, (unsigned long long)c);
+    }
+}
+
+__global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCodec p, const QTable qt,
+                                                                  int task_begin) {
+    const SegTask T = p.tasks[task_begin + blockIdx.y];
+    const int N = p.N, bpr = N / 8;
+    const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
+    int c = 0;
+    if (blk < ((T.r1 - T.r0) / 8) * bpr) {
+        const int kk = *p.iter;
+        const size_t n = (size_t)N * N;
+        const int bi = blk / bpr, bj = blk - bi * bpr;
+        const size_t o = (size_t)T.slice * n + (size_t)(T.r0 + bi * 8) * N + (size_t)bj * 8;
+        const int slot = (kk + 1) % p.D;
+        float* dst = p.hist + ((size_t)slot * 3 + DADMM_Q_JPEG) * p.S * n + o;
+        const float lo = key_float(p.lo_key[T.slice * p.M + T.owner]);
+        const float hi = key_float(p.hi_key[T.slice * p.M + T.owner]);
+        if (hi > lo)
+            c = jpeg_block(p.xseg + o, dst, N, lo, hi, qt, nullptr);
+        else
+            jpeg_const_block(dst, N, lo);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd((unsigned long long*)(p.nnz + T.slice * p.M + T.owner), (unsigned long long)c);
+}
+
+static float* lohi_scratch() {
+    static std::mutex mu;
+    static std::vector<float*> bufs;
+    int dev = 0;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)bufs.size() <= dev) bufs.resize(dev + 1, nullptr);
+    if (!bufs[dev]) TOMO_CUDA(cudaMalloc(&bufs[dev], 256));  // once per device, held until exit
+    return bufs[dev];
+}
+
+void launch_jpeg_single(const float* in, int rows, int cols, int quality, int16_t* coefs, float* lohi,
+                        float* deq, long long* nnz, cudaStream_t st) {
+    ensure_dct_table();
+    float* lh = lohi ? lohi : lohi_scratch();
+    minmax_kernel<<<1, 1024, 0, st>>>(in, (long long)rows * cols, lh);
+    TOMO_CUDA(cudaGetLastError());
+    QTable qt;
+    jpeg_quant_table(quality, qt.q);
+    const int nblk = (rows / 8) * (cols / 8);
+    jpeg_single_kernel<<<ceil_div(nblk, kJpegThreads), kJpegThreads, 0, st>>>(in, rows, cols, qt, coefs, lh,
+                                                                              deq, nnz);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+void launch_jpeg_dadmm(const DadmmCodec& p, int quality, int max_rows, int task_begin, int task_count,
+                       cudaStream_t st) {
+    if (task_count <= 0) return;
+    ensure_dct_table();
+    QTable qt;
+    jpeg_quant_table(quality, qt.q);
+    const int nblk = (max_rows / 8) * (p.N / 8);
+    dim3 grid(ceil_div(nblk, kJpegThreads), task_count);
+    jpeg_dadmm_kernel<<<grid, kJpegThreads, 0, st>>>(p, qt, task_begin);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+// everything that must not run while a stream is being captured
+void prepare_codecs(int km_k) {
+    ensure_dct_table();
+    with_kmax(km_k < 1 ? 1 : km_k, [&](auto KM) {
+        constexpr int KMAX = decltype(KM)::value;
+        TOMO_CUDA(cudaFuncSetAttribute(kmeans_dadmm_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kmeans_smem(KMAX)));
+    });
+}
+
+}  // namespace tomo
+
+using namespace tomo;
+
+extern "C" {
+
+uint64_t quant_kmeans_key(uint64_t seed, int slice, int owner, int iteration) {
+    return tomo::kmeans_key(seed, slice, owner, iteration);
+}
+
+tomo_status quant_kmeans(const float* in, int64_t n, int k, int iters, uint64_t key, uint8_t* codes,
+                         float* centroids, float* deq, double* objective, tomo_stream_t stream) {
+    return guard([&] {
+        TOMO_REQUIRE(in && deq, "in and deq must be non-NULL");
+        TOMO_REQUIRE(n >= 1 && n <= (int64_t)1 << 40, "n out of range");
+        TOMO_REQUIRE(k >= 1 && k <= kKmMaxK, "k must be in [1, 32]");
+        TOMO_REQUIRE(iters >= 0 && iters <= 10000, "iters out of range");
+        launch_kmeans_single(in, n, k, iters, key, codes, centroids, deq, objective, (cudaStream_t)stream);
+    });
+}
+
+tomo_status quant_jpeg(const float* in, int rows, int cols, int quality, int16_t* coefs, float* lohi,
+                       float* deq, int64_t* nnz, tomo_stream_t stream) {
+    return guard([&] {
+        TOMO_REQUIRE(in && deq, "in and deq must be non-NULL");
+        TOMO_REQUIRE(rows >= 8 && cols >= 8 && rows % 8 == 0 && cols % 8 == 0,
+                     "rows and cols must be positive multiples of 8");
+        TOMO_REQUIRE(quality >= 1 && quality <= 100, "quality must be in [1, 100]");
+        TOMO_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)deq % 16) == 0,
+                     "in and deq must be 16-byte aligned");
+        launch_jpeg_single(in, rows, cols, quality, coefs, lohi, deq, (long long*)nnz, (cudaStream_t)stream);
+    });
+}
+
+}  // extern "C"

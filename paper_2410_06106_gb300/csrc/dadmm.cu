@@ -1,0 +1,963 @@
+// Decentralized ADMM with quantized messages (Sec. 2.4-2.7, Algorithms 2-4,
+// Eq. 15-18 and 21-24) for S independent slices of M simulated nodes on one
+// GB300.
+//
+// One iteration:
+//   E1 x [ projector + residual  (persistent kernel over every (slice, node,
+//          angle group, bin run) item)
+//        | backprojector + fused u-step (persistent kernel over every
+//          (slice, node, 64x32 tile) item) ]                 Algorithm 2
+//   x-step on every owner's segment + identity messages + segment min/max
+//                                                               Algorithm 3
+//   K-means messages (one CTA per owner) and JPEG messages      Eq. 23
+//   dual update of every node against its view of x + FP64 partial norms
+//                                                               Eq. 24
+//   statistics and the iteration counter
+//
+// Message graph (the paper sends every segment to every node, Sec. 2.5;
+// here any connected graph): segment s reaches node m along the shortest
+// path with lowest-id parents, one hop per iteration, relayed verbatim, so
+// node m's view of segment s at iteration k is the message of iteration
+// k - max(dist(s,m) - 1, 0) through the quantizer of the path's first edge.
+// Messages live in a ring hist[D][kind][S][N][N] that every reader indexes
+// with (k - lag) mod D; the iteration counter lives on the device so one
+// captured CUDA graph serves every iteration.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <queue>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+void prepare_codecs(int km_k);
+
+constexpr int kStatsCap = 1024;   // statistics ring (iterations)
+constexpr int kDualPerNode = 8;   // dual-kernel blocks per (slice, node)
+constexpr int kResPerSlice = 64;  // residual-norm blocks per slice
+constexpr int kElemThreads = 256;
+
+struct Dadmm {
+    Geometry* g = nullptr;
+    int N = 0, B = 0, A = 0, S = 0, M = 0, D = 1;
+    int E1 = 0, E2 = 0, km_k = 0, km_iters = 0, jpeg_q = 50, mode = 0;
+    double rho = 1.0, eta2 = 0.0;
+    uint64_t seed = 0;
+    std::vector<int32_t> seg_row_ptr, home_q;
+    std::vector<int8_t> lag, kind;  // [node][segment]
+    std::vector<int32_t> recv_cnt;  // [owner][3]: receivers of each kind
+    std::vector<int32_t> need;      // [owner]: bitmask of message kinds produced
+    // device tables
+    AngRow* d_angs = nullptr;
+    ProjItem* d_pitems = nullptr;   // batched order (longest first)
+    BpItem* d_bitems = nullptr;
+    ProjItem* d_pplain = nullptr;   // grouped by (slice, node)
+    BpItem* d_bplain = nullptr;
+    int n_pitems = 0, n_bitems = 0;
+    std::vector<int> p_range, b_range;  // [(slice*M + node) * 2]: begin, end in the plain lists
+    int8_t* d_lag = nullptr;
+    int8_t* d_kind = nullptr;
+    int32_t* d_seg_of_row = nullptr;
+    int32_t* d_need = nullptr;
+    int32_t* d_recv = nullptr;
+    int32_t* d_home = nullptr;
+    float* d_eta1 = nullptr;
+    SegTask* d_km = nullptr;
+    SegTask* d_jp = nullptr;
+    int n_km = 0, n_jp = 0, max_jp_rows = 0;
+    std::vector<int> km_slice_begin, jp_slice_begin;  // tasks are slice-major: per-(slice, owner) index
+    std::vector<int> km_index, jp_index;              // [(slice*M + owner)] -> task index or -1
+    int grid_proj = 0, grid_bp = 0;
+    // workspace layout (byte offsets from the aligned base)
+    size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_dual = 0,
+           off_res = 0, off_stats = 0, off_status = 0, ws_bytes = 0;
+    // stream / graph
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> gkey;
+    // phase timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> pev;  // num_phases + 1 boundaries
+    int num_phases() const { return 2 * E1 + 5; }
+};
+
+static Dadmm* as_dadmm(dadmm_t h) {
+    TOMO_REQUIRE(h != nullptr, "dadmm handle is NULL");
+    return reinterpret_cast<Dadmm*>(h);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------
+struct ElemParams {
+    float* u;      // [S][M][N][N]
+    float* lam;    // [S][M][N][N]
+    float* xseg;   // [S][N][N]
+    float* hist;   // [D][3][S][N][N]
+    int32_t* iter;
+    const int32_t* seg_of_row;
+    const int8_t* lag;
+    const int8_t* kind;
+    const int32_t* need;
+    unsigned* lo_key;
+    unsigned* hi_key;
+    double* dual_part;  // [S][M*kDualPerNode][3]
+    int N, S, M, D, E2;
+    float rho, eta2rho, inv_rho;
+};
+
+// Algorithm 3 on every row of every owner's segment, E2 steps in registers:
+// x <- x - eta2 rho (x - u_m - lambda_m / rho); then the identity message and
+// the segment's min / max (JPEG sample map)
+__global__ void __launch_bounds__(kElemThreads) xstep_kernel(const ElemParams p, int row_begin, int row_count) {
+    __shared__ float s_lo[kElemThreads / 32], s_hi[kElemThreads / 32];
+    const int N = p.N;
+    const size_t n = (size_t)N * N;
+    const int k = *p.iter;
+    const int slot = (k + 1) % p.D;
+    for (int rr = blockIdx.x; rr < row_count; rr += gridDim.x) {
+        const int R = row_begin + rr;  // global row: slice * N + i
+        const int slice = R / N, i = R - slice * N;
+        const int m = p.seg_of_row[i];
+        const size_t ro = (size_t)i * N;
+        const float* u = p.u + ((size_t)slice * p.M + m) * n + ro;
+        const float* l = p.lam + ((size_t)slice * p.M + m) * n + ro;
+        float* x = p.xseg + (size_t)slice * n + ro;
+        float* xid = (p.need[m] & 1) ? p.hist + ((size_t)slot * 3 + DADMM_Q_NONE) * p.S * n + (size_t)slice * n + ro
+                                     : nullptr;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int j = threadIdx.x; j < N; j += kElemThreads) {
+            const float v = fmaf(l[j], p.inv_rho, u[j]);  // u + lambda / rho
+            float xv = x[j];
+            for (int e = 0; e < p.E2; ++e) xv = fmaf(-p.eta2rho, xv - v, xv);
+            x[j] = xv;
+            if (xid) xid[j] = xv;
+            lo = fminf(lo, xv);
+            hi = fmaxf(hi, xv);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_lo[threadIdx.x >> 5] = lo;
+            s_hi[threadIdx.x >> 5] = hi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kElemThreads / 32; ++w) {
+                lo = fminf(lo, s_lo[w]);
+                hi = fmaxf(hi, s_hi[w]);
+            }
+            atomicMin(p.lo_key + slice * p.M + m, float_key(lo));
+            atomicMax(p.hi_key + slice * p.M + m, float_key(hi));
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ const float* view_row(const ElemParams& p, int slice, int m, int i, int k) {
+    const int seg = p.seg_of_row[i];
+    const int mi = m * p.M + seg;
+    const int j = k - p.lag[mi];
+    if (j < 1) return nullptr;
+    const size_t n = (size_t)p.N * p.N;
+    return p.hist + (((size_t)(j % p.D) * 3 + p.kind[mi]) * p.S + slice) * n + (size_t)i * p.N;
+}
+
+// Eq. 24 on every node: lambda_m <- lambda_m + rho (u_m - x_m^{k+1}); FP64
+// partial norms per block (gap2 over all nodes; change and norm of node 0's view)
+__global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, int node_begin, int slice_begin) {
+    __shared__ double s_red[3][kElemThreads / 32];
+    const int N = p.N;
+    const size_t n = (size_t)N * N;
+    const int k = *p.iter;
+    const int slice = slice_begin + blockIdx.y;
+    const int node = node_begin + blockIdx.x / kDualPerNode;
+    const int part = blockIdx.x % kDualPerNode;
+    double gap = 0.0, chg = 0.0, nrm = 0.0;
+    for (int i = part; i < N; i += kDualPerNode) {
+        const size_t o = ((size_t)slice * p.M + node) * n + (size_t)i * N;
+        const float* u = p.u + o;
+        float* l = p.lam + o;
+        const float* x1 = view_row(p, slice, node, i, k + 1);
+        const float* x0 = node == 0 ? view_row(p, slice, node, i, k) : nullptr;
+        float g = 0.f, c = 0.f, q = 0.f;
+        for (int j = threadIdx.x; j < N; j += kElemThreads) {
+            const float xv = x1 ? x1[j] : 0.f;
+            const float pr = u[j] - xv;
+            g = fmaf(pr, pr, g);
+            l[j] = fmaf(p.rho, pr, l[j]);
+            if (node == 0) {
+                const float xo = x0 ? x0[j] : 0.f;
+                c = fmaf(xv - xo, xv - xo, c);
+                q = fmaf(xo, xo, q);
+            }
+        }
+        gap += g;
+        chg += c;
+        nrm += q;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        gap += __shfl_xor_sync(0xffffffffu, gap, o);
+        chg += __shfl_xor_sync(0xffffffffu, chg, o);
+        nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_red[0][w] = gap;
+        s_red[1][w] = chg;
+        s_red[2][w] = nrm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int v = 0; v < kElemThreads / 32; ++v) {
+            a += s_red[0][v];
+            b += s_red[1][v];
+            c += s_red[2][v];
+        }
+        double* d = p.dual_part + (((size_t)slice * p.M + node) * kDualPerNode + part) * 3;
+        d[0] = a;
+        d[1] = b;
+        d[2] = c;
+    }
+}
+
+// sum of squared residuals (last inner step) per slice
+__global__ void __launch_bounds__(kElemThreads) resid_kernel(const float* resid, int A, int B, double* part) {
+    __shared__ double s_red[kElemThreads / 32];
+    const int slice = blockIdx.y;
+    double acc = 0.0;
+    for (int a = blockIdx.x; a < A; a += kResPerSlice) {
+        const float* r = resid + ((size_t)slice * A + a) * B;
+        float t = 0.f;
+        for (int b = threadIdx.x; b < B; b += kElemThreads) t = fmaf(r[b], r[b], t);
+        acc += t;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kElemThreads / 32; ++w) t += s_red[w];
+        part[(size_t)slice * kResPerSlice + blockIdx.x] = t;
+    }
+}
+
+struct FinParams {
+    const double* dual_part;
+    const double* res_part;
+    const long long* nnz;      // [S][M]
+    const int32_t* recv;       // [M][3]
+    const int32_t* seg_rows;   // [M]
+    double* stats;             // [kStatsCap][S][DADMM_NSTAT]
+    int32_t* iter;
+    int* status;
+    int S, M, N, km_k;
+};
+
+// deterministic reduction of the partials, message bytes, counter increment
+__global__ void finalize_kernel(const FinParams p) {
+    __shared__ double s[4][256];
+    const int k = *p.iter;
+    for (int slice = 0; slice < p.S; ++slice) {
+        double a = 0.0, b = 0.0, c = 0.0, r = 0.0, by = 0.0;
+        const int nparts = p.M * kDualPerNode;
+        for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+            const double* d = p.dual_part + ((size_t)slice * nparts + q) * 3;
+            a += d[0];
+            b += d[1];
+            c += d[2];
+        }
+        for (int q = threadIdx.x; q < kResPerSlice; q += blockDim.x) r += p.res_part[(size_t)slice * kResPerSlice + q];
+        int bits = 0;
+        while ((1 << bits) < p.km_k) ++bits;
+        for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
+            const double len = (double)p.seg_rows[m] * p.N;
+            by += p.recv[m * 3 + 0] * 4.0 * len;
+            by += p.recv[m * 3 + 1] * (bits * len / 8.0 + 4.0 * p.km_k);
+            by += p.recv[m * 3 + 2] * (2.0 * (double)p.nnz[slice * p.M + m] + 8.0);
+        }
+        s[0][threadIdx.x] = a;
+        s[1][threadIdx.x] = b;
+        s[2][threadIdx.x] = c;
+        s[3][threadIdx.x] = r;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w)
+                for (int t = 0; t < 4; ++t) s[t][threadIdx.x] += s[t][threadIdx.x + w];
+            __syncthreads();
+        }
+        // bytes: exact integers in double, any order
+        for (int o = 16; o > 0; o >>= 1) by += __shfl_xor_sync(0xffffffffu, by, o);
+        __shared__ double s_by[8];
+        if ((threadIdx.x & 31) == 0) s_by[threadIdx.x >> 5] = by;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tb = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tb += s_by[w];
+            double* st = p.stats + ((size_t)(k % kStatsCap) * p.S + slice) * DADMM_NSTAT;
+            st[0] = s[0][0];
+            st[1] = s[1][0];
+            st[2] = s[2][0];
+            st[3] = s[3][0];
+            st[4] = tb;
+            for (int t = 0; t < 4; ++t)
+                if (!isfinite(s[t][0])) atomicOr(p.status, 2);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *p.iter = k + 1;
+}
+
+__global__ void home_view_kernel(const float* hist, const int32_t* iter, const int32_t* seg_of_row,
+                                 const int32_t* home, float* out, int N, int S, int D) {
+    const size_t n = (size_t)N * N;
+    const int k = *iter;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)S * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int slice = (int)(e / n);
+        const size_t o = e - (size_t)slice * n;
+        const int i = (int)(o / N);
+        if (k < 1) {
+            out[e] = 0.f;
+            continue;
+        }
+        const int m = seg_of_row[i];
+        out[e] = hist[(((size_t)(k % D) * 3 + home[m]) * S + slice) * n + o];
+    }
+}
+
+// ------------------------------------------------------------------
+// host
+// ------------------------------------------------------------------
+static void relay_tables(int M, const std::vector<int32_t>& adj, std::vector<int>& dist,
+                         std::vector<int>& first) {
+    dist.assign((size_t)M * M, -1);
+    first.assign((size_t)M * M, -1);
+    for (int s = 0; s < M; ++s) {
+        int* d = &dist[(size_t)s * M];
+        std::queue<int> q;
+        d[s] = 0;
+        q.push(s);
+        while (!q.empty()) {
+            const int x = q.front();
+            q.pop();
+            for (int y = 0; y < M; ++y)
+                if (adj[(size_t)x * M + y] && d[y] < 0) {
+                    d[y] = d[x] + 1;
+                    q.push(y);
+                }
+        }
+        for (int m = 0; m < M; ++m) {
+            if (m == s) {
+                first[(size_t)s * M + m] = s;
+                continue;
+            }
+            if (d[m] < 0) continue;
+            int cur = m;
+            while (d[cur] > 1) {  // lowest-id neighbour one hop closer to s
+                int par = -1;
+                for (int pp = 0; pp < M && par < 0; ++pp)
+                    if (adj[(size_t)pp * M + cur] && d[pp] == d[cur] - 1) par = pp;
+                cur = par;
+            }
+            first[(size_t)s * M + m] = cur;
+        }
+    }
+}
+
+static void free_dadmm(Dadmm* h) {
+    if (!h) return;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->own) cudaStreamDestroy(h->own);
+    for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+    void* ptrs[] = {h->d_angs, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
+                    h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_km, h->d_jp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+struct WsPtrs {
+    float* resid;
+    int* counters;
+    unsigned* lo;
+    unsigned* hi;
+    long long* nnz;
+    double* dual;
+    double* res;
+    double* stats;
+    int* status;
+};
+
+static WsPtrs ws_ptrs(const Dadmm& h, void* ws) {
+    char* b = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    WsPtrs w;
+    w.resid = (float*)(b + h.off_resid);
+    w.counters = (int*)(b + h.off_counters);
+    w.lo = (unsigned*)(b + h.off_lo);
+    w.hi = (unsigned*)(b + h.off_hi);
+    w.nnz = (long long*)(b + h.off_nnz);
+    w.dual = (double*)(b + h.off_dual);
+    w.res = (double*)(b + h.off_res);
+    w.stats = (double*)(b + h.off_stats);
+    w.status = (int*)(b + h.off_status);
+    return w;
+}
+
+static ElemParams elem_params(const Dadmm& h, const dadmm_state& st, const WsPtrs& w) {
+    ElemParams p{};
+    p.u = st.u;
+    p.lam = st.lam;
+    p.xseg = st.xseg;
+    p.hist = st.hist;
+    p.iter = st.iter;
+    p.seg_of_row = h.d_seg_of_row;
+    p.lag = h.d_lag;
+    p.kind = h.d_kind;
+    p.need = h.d_need;
+    p.lo_key = w.lo;
+    p.hi_key = w.hi;
+    p.dual_part = w.dual;
+    p.N = h.N;
+    p.S = h.S;
+    p.M = h.M;
+    p.D = h.D;
+    p.E2 = h.E2;
+    p.rho = (float)h.rho;
+    p.eta2rho = (float)(h.eta2 * h.rho);
+    p.inv_rho = (float)(1.0 / h.rho);
+    return p;
+}
+
+// enqueue one full iteration on stream st
+static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w,
+                              cudaStream_t s) {
+    const bool batched = h.mode == DADMM_MODE_BATCHED;
+    int phase = 0;
+    auto mark = [&]() {  // boundary before phase `phase`
+        if (h.profiling) TOMO_CUDA(cudaEventRecord(h.pev[phase], s));
+        ++phase;
+    };
+    const size_t SM = (size_t)h.S * h.M;
+    // per-iteration resets: work queues, segment min/max keys, JPEG counters
+    TOMO_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * (2 * h.E1 + 2), s));
+    TOMO_CUDA(cudaMemsetAsync(w.lo, 0xFF, sizeof(unsigned) * SM, s));
+    TOMO_CUDA(cudaMemsetAsync(w.hi, 0x00, sizeof(unsigned) * SM, s));
+    TOMO_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(long long) * SM, s));
+
+    ProjParams pp{};
+    pp.img = st.u;
+    pp.out = w.resid;
+    pp.sub = sino;
+    pp.angs = h.d_angs;
+    pp.status = w.status;
+    pp.N = h.N;
+    pp.B = h.B;
+    pp.const_off = h.g->const_off;
+    BpParams bp{};
+    bp.sino = w.resid;
+    bp.angs = h.d_angs;
+    bp.status = w.status;
+    bp.N = h.N;
+    bp.B = h.B;
+    bp.const_off = h.g->const_off;
+    bp.view.hist = st.hist;
+    bp.view.iter = st.iter;
+    bp.view.lag = h.d_lag;
+    bp.view.kind = h.d_kind;
+    bp.view.seg_of_row = h.d_seg_of_row;
+    bp.view.eta1 = h.d_eta1;
+    bp.view.u = st.u;
+    bp.view.lam = st.lam;
+    bp.view.rho = (float)h.rho;
+    bp.view.D = h.D;
+    bp.view.S = h.S;
+    bp.view.M = h.M;
+
+    for (int e = 0; e < h.E1; ++e) {
+        if (batched) {
+            mark();
+            pp.items = h.d_pitems;
+            pp.n_items = h.n_pitems;
+            pp.counter = w.counters + 2 * e;
+            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s);
+            mark();
+            bp.items = h.d_bitems;
+            bp.n_items = h.n_bitems;
+            bp.counter = w.counters + 2 * e + 1;
+            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s);
+        } else {
+            mark();
+            for (int sn = 0; sn < h.S * h.M; ++sn) {
+                pp.items = h.d_pplain + h.p_range[2 * sn];
+                pp.n_items = h.p_range[2 * sn + 1] - h.p_range[2 * sn];
+                pp.counter = nullptr;
+                launch_project(pp, pp.n_items, s);
+            }
+            mark();
+            for (int sn = 0; sn < h.S * h.M; ++sn) {
+                bp.items = h.d_bplain + h.b_range[2 * sn];
+                bp.n_items = h.b_range[2 * sn + 1] - h.b_range[2 * sn];
+                bp.counter = nullptr;
+                launch_backproject_ustep(bp, bp.n_items, s);
+            }
+        }
+    }
+
+    ElemParams ep = elem_params(h, st, w);
+    DadmmCodec cp{};
+    cp.xseg = st.xseg;
+    cp.hist = st.hist;
+    cp.iter = st.iter;
+    cp.N = h.N;
+    cp.S = h.S;
+    cp.D = h.D;
+    cp.seed = h.seed;
+    cp.lo_key = w.lo;
+    cp.hi_key = w.hi;
+    cp.nnz = w.nnz;
+    cp.M = h.M;
+    if (batched) {
+        const int rows = h.S * h.N;
+        mark();
+        xstep_kernel<<<std::min(rows, 152 * 8), kElemThreads, 0, s>>>(ep, 0, rows);
+        TOMO_CUDA(cudaGetLastError());
+        mark();
+        cp.tasks = h.d_km;
+        launch_kmeans_dadmm(cp, h.km_k, h.km_iters, 0, h.n_km, s);
+        mark();
+        cp.tasks = h.d_jp;
+        launch_jpeg_dadmm(cp, h.jpeg_q, h.max_jp_rows, 0, h.n_jp, s);
+        mark();
+        dual_kernel<<<dim3(h.M * kDualPerNode, h.S), kElemThreads, 0, s>>>(ep, 0, 0);
+        TOMO_CUDA(cudaGetLastError());
+    } else {
+        mark();
+        for (int sl = 0; sl < h.S; ++sl)
+            for (int m = 0; m < h.M; ++m) {
+                const int r0 = h.seg_row_ptr[m], r1 = h.seg_row_ptr[m + 1];
+                xstep_kernel<<<r1 - r0, kElemThreads, 0, s>>>(ep, sl * h.N + r0, r1 - r0);
+                TOMO_CUDA(cudaGetLastError());
+            }
+        mark();
+        cp.tasks = h.d_km;
+        for (int sl = 0; sl < h.S; ++sl)
+            for (int m = 0; m < h.M; ++m) {
+                const int ki = h.km_index[sl * h.M + m];
+                if (ki >= 0) launch_kmeans_dadmm(cp, h.km_k, h.km_iters, ki, 1, s);
+            }
+        mark();
+        cp.tasks = h.d_jp;
+        for (int sl = 0; sl < h.S; ++sl)
+            for (int m = 0; m < h.M; ++m) {
+                const int ji = h.jp_index[sl * h.M + m];
+                if (ji >= 0) launch_jpeg_dadmm(cp, h.jpeg_q, h.seg_row_ptr[m + 1] - h.seg_row_ptr[m], ji, 1, s);
+            }
+        mark();
+        for (int sl = 0; sl < h.S; ++sl)
+            for (int m = 0; m < h.M; ++m) {
+                dual_kernel<<<dim3(kDualPerNode, 1), kElemThreads, 0, s>>>(ep, m, sl);
+                TOMO_CUDA(cudaGetLastError());
+            }
+    }
+    mark();
+    resid_kernel<<<dim3(kResPerSlice, h.S), kElemThreads, 0, s>>>(w.resid, h.A, h.B, w.res);
+    TOMO_CUDA(cudaGetLastError());
+    FinParams fp{};
+    fp.dual_part = w.dual;
+    fp.res_part = w.res;
+    fp.nnz = w.nnz;
+    fp.recv = h.d_recv;
+    fp.seg_rows = h.d_need + h.M;  // second half of the need table holds the segment row counts
+    fp.stats = w.stats;
+    fp.iter = st.iter;
+    fp.status = w.status;
+    fp.S = h.S;
+    fp.M = h.M;
+    fp.N = h.N;
+    fp.km_k = h.km_k;
+    finalize_kernel<<<1, 256, 0, s>>>(fp);
+    TOMO_CUDA(cudaGetLastError());
+    mark();  // end of the last phase
+}
+
+}  // namespace tomo
+
+using namespace tomo;
+
+extern "C" {
+
+tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* out) {
+    return guard([&] {
+        TOMO_REQUIRE(out != nullptr && cfg != nullptr, "cfg and out must be non-NULL");
+        *out = nullptr;
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        const dadmm_config& c = *cfg;
+        TOMO_REQUIRE(c.N == g->N && c.n_bins == g->B && c.n_angles == g->A,
+                     "config sizes differ from the geometry");
+        TOMO_REQUIRE(c.S >= 1 && c.M >= 1 && c.M <= 127, "need S >= 1 and 1 <= M <= 127");
+        TOMO_REQUIRE(c.node_ang_ptr && c.node_ang && c.seg_row_ptr && c.adj && c.edge_q && c.home_q && c.eta1,
+                     "config arrays must be non-NULL");
+        TOMO_REQUIRE(c.E1 >= 0 && c.E1 <= 1000 && c.E2 >= 0 && c.E2 <= 100000, "E1/E2 out of range");
+        TOMO_REQUIRE(c.rho > 0.0 && std::isfinite(c.rho), "rho must be positive");
+        TOMO_REQUIRE(c.mode == DADMM_MODE_BATCHED || c.mode == DADMM_MODE_PLAIN, "unknown mode");
+        const int M = c.M, N = c.N, A = c.n_angles;
+        // angle partition
+        TOMO_REQUIRE(c.node_ang_ptr[0] == 0 && c.node_ang_ptr[M] == A, "node_ang_ptr must span all angles");
+        std::vector<int> seen(A, 0);
+        for (int m = 0; m < M; ++m) {
+            TOMO_REQUIRE(c.node_ang_ptr[m + 1] >= c.node_ang_ptr[m], "node_ang_ptr must be non-decreasing");
+            for (int q = c.node_ang_ptr[m]; q < c.node_ang_ptr[m + 1]; ++q) {
+                const int a = c.node_ang[q];
+                TOMO_REQUIRE(a >= 0 && a < A && !seen[a], "node_ang must be a permutation of the angles");
+                seen[a] = 1;
+            }
+        }
+        TOMO_REQUIRE(c.seg_row_ptr[0] == 0 && c.seg_row_ptr[M] == N, "seg_row_ptr must span the rows");
+        for (int m = 0; m < M; ++m)
+            TOMO_REQUIRE(c.seg_row_ptr[m + 1] > c.seg_row_ptr[m], "every segment needs at least one row");
+        std::vector<int32_t> adj(c.adj, c.adj + (size_t)M * M);
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b)
+                TOMO_REQUIRE(adj[(size_t)a * M + b] == adj[(size_t)b * M + a] && (a != b || !adj[(size_t)a * M + a]),
+                             "adj must be symmetric with an empty diagonal");
+        std::vector<int> dist, first;
+        relay_tables(M, adj, dist, first);
+        int max_lag = 0;
+        for (int v : dist) {
+            TOMO_REQUIRE(v >= 0, "the message graph must be connected");
+            max_lag = std::max(max_lag, v - 1);
+        }
+        TOMO_REQUIRE(max_lag <= 125, "graph diameter too large");
+
+        auto* h = new Dadmm();
+        try {
+            h->g = g;
+            h->N = N;
+            h->B = c.n_bins;
+            h->A = A;
+            h->S = c.S;
+            h->M = M;
+            h->D = max_lag + 2;  // ring also keeps node 0's previous view for the change statistic
+            h->E1 = c.E1;
+            h->E2 = c.E2;
+            h->rho = c.rho;
+            h->eta2 = c.eta2;
+            h->km_k = c.km_k;
+            h->km_iters = c.km_iters;
+            h->jpeg_q = c.jpeg_quality;
+            h->seed = c.seed;
+            h->mode = c.mode;
+            h->seg_row_ptr.assign(c.seg_row_ptr, c.seg_row_ptr + M + 1);
+            h->home_q.assign(c.home_q, c.home_q + M);
+            // kinds
+            h->lag.assign((size_t)M * M, 0);
+            h->kind.assign((size_t)M * M, 0);
+            h->recv_cnt.assign((size_t)M * 3, 0);
+            h->need.assign((size_t)M, 0);
+            for (int m = 0; m < M; ++m) {
+                TOMO_REQUIRE(h->home_q[m] >= 0 && h->home_q[m] <= 2, "home_q must be a DADMM_Q_* value");
+                h->need[m] |= 1 << h->home_q[m];
+            }
+            for (int s = 0; s < M; ++s)
+                for (int m = 0; m < M; ++m) {
+                    int kd;
+                    if (s == m) {
+                        kd = h->home_q[m];
+                        h->lag[(size_t)m * M + s] = 0;
+                    } else {
+                        const int f = first[(size_t)s * M + m];
+                        kd = c.edge_q[(size_t)s * M + f];
+                        TOMO_REQUIRE(kd >= 0 && kd <= 2, "edge_q must be a DADMM_Q_* value on every edge");
+                        h->lag[(size_t)m * M + s] = (int8_t)(dist[(size_t)s * M + m] - 1);
+                        h->recv_cnt[(size_t)s * 3 + kd] += 1;
+                        h->need[s] |= 1 << kd;
+                    }
+                    h->kind[(size_t)m * M + s] = (int8_t)kd;
+                }
+            bool any_km = false, any_jp = false;
+            for (int m = 0; m < M; ++m) {
+                any_km |= (h->need[m] >> 1) & 1;
+                any_jp |= (h->need[m] >> 2) & 1;
+                if ((h->need[m] >> 2) & 1)
+                    TOMO_REQUIRE((h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]) % 8 == 0 && N % 8 == 0,
+                                 "JPEG segments need row counts and N that are multiples of 8");
+            }
+            if (any_km) TOMO_REQUIRE(c.km_k >= 1 && c.km_k <= kKmMaxK && c.km_iters >= 0, "bad K-means settings");
+            if (any_jp) TOMO_REQUIRE(c.jpeg_quality >= 1 && c.jpeg_quality <= 100, "bad JPEG quality");
+            for (int m = 0; m < M; ++m)
+                TOMO_REQUIRE(std::isfinite(c.eta1[m]) && c.eta1[m] > 0.0, "eta1 must be positive");
+
+            // angle list (node-major), rows = natural angle index
+            std::vector<AngRow> angs(A);
+            for (int q = 0; q < A; ++q) angs[q] = AngRow{c.node_ang[q], c.node_ang[q]};
+            // work lists
+            std::vector<ProjItem> pplain;
+            std::vector<BpItem> bplain;
+            h->p_range.resize((size_t)2 * c.S * M);
+            h->b_range.resize((size_t)2 * c.S * M);
+            for (int sl = 0; sl < c.S; ++sl)
+                for (int m = 0; m < M; ++m) {
+                    const int a0 = c.node_ang_ptr[m], na = c.node_ang_ptr[m + 1] - a0;
+                    const int sn = sl * M + m;
+                    h->p_range[2 * sn] = (int)pplain.size();
+                    if (na > 0) build_proj_items(*g, angs, a0, na, sn, sl * A, pplain);
+                    h->p_range[2 * sn + 1] = (int)pplain.size();
+                    h->b_range[2 * sn] = (int)bplain.size();
+                    if (na > 0) build_bp_items(*g, a0, na, sn, sl * A, m, sl, bplain);
+                    h->b_range[2 * sn + 1] = (int)bplain.size();
+                }
+            // nodes without angles still need the u-step (pure proximal term)
+            for (int sl = 0; sl < c.S; ++sl)
+                for (int m = 0; m < M; ++m) {
+                    const int sn = sl * M + m;
+                    if (h->b_range[2 * sn] == h->b_range[2 * sn + 1]) {
+                        build_bp_items(*g, c.node_ang_ptr[m], 0, sn, sl * A, m, sl, bplain);
+                        h->b_range[2 * sn + 1] = (int)bplain.size();
+                    }
+                }
+            std::vector<ProjItem> pb = pplain;
+            std::vector<BpItem> bb = bplain;
+            std::stable_sort(pb.begin(), pb.end(), [](const ProjItem& x, const ProjItem& y) {
+                return x.nchunks * x.na > y.nchunks * y.na;
+            });
+            std::stable_sort(bb.begin(), bb.end(), [](const BpItem& x, const BpItem& y) { return x.na > y.na; });
+            h->d_angs = device_upload(angs);
+            h->d_pitems = device_upload(pb);
+            h->d_bitems = device_upload(bb);
+            h->d_pplain = device_upload(pplain);
+            h->d_bplain = device_upload(bplain);
+            h->n_pitems = (int)pb.size();
+            h->n_bitems = (int)bb.size();
+            // tables
+            std::vector<int32_t> seg_of_row(N);
+            for (int m = 0; m < M; ++m)
+                for (int i = h->seg_row_ptr[m]; i < h->seg_row_ptr[m + 1]; ++i) seg_of_row[i] = m;
+            h->d_lag = device_upload(h->lag);
+            h->d_kind = device_upload(h->kind);
+            h->d_seg_of_row = device_upload(seg_of_row);
+            std::vector<int32_t> need2(h->need);
+            for (int m = 0; m < M; ++m) need2.push_back(h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]);
+            h->d_need = device_upload(need2);
+            h->d_recv = device_upload(h->recv_cnt);
+            h->d_home = device_upload(h->home_q);
+            std::vector<float> eta(M);
+            for (int m = 0; m < M; ++m) eta[m] = (float)c.eta1[m];
+            h->d_eta1 = device_upload(eta);
+            // codec tasks, slice-major
+            std::vector<SegTask> km, jp;
+            h->km_index.assign((size_t)c.S * M, -1);
+            h->jp_index.assign((size_t)c.S * M, -1);
+            for (int sl = 0; sl < c.S; ++sl)
+                for (int m = 0; m < M; ++m) {
+                    const SegTask t{sl, m, h->seg_row_ptr[m], h->seg_row_ptr[m + 1]};
+                    if ((h->need[m] >> 1) & 1) {
+                        h->km_index[(size_t)sl * M + m] = (int)km.size();
+                        km.push_back(t);
+                    }
+                    if ((h->need[m] >> 2) & 1) {
+                        h->jp_index[(size_t)sl * M + m] = (int)jp.size();
+                        jp.push_back(t);
+                        h->max_jp_rows = std::max(h->max_jp_rows, t.r1 - t.r0);
+                    }
+                }
+            h->d_km = device_upload(km);
+            h->d_jp = device_upload(jp);
+            h->n_km = (int)km.size();
+            h->n_jp = (int)jp.size();
+            // launch shapes
+            h->grid_proj = persistent_grid_project();
+            h->grid_bp = persistent_grid_backproject(true);
+            prepare_codecs(c.km_k);
+            // workspace layout
+            size_t off = 0;
+            auto take = [&](size_t bytes) {
+                const size_t o = off;
+                off = align256(off + bytes);
+                return o;
+            };
+            const size_t SMn = (size_t)c.S * M;
+            h->off_resid = take(sizeof(float) * (size_t)c.S * A * c.n_bins);
+            h->off_counters = take(sizeof(int) * (2 * (size_t)c.E1 + 2));
+            h->off_lo = take(sizeof(unsigned) * SMn);
+            h->off_hi = take(sizeof(unsigned) * SMn);
+            h->off_nnz = take(sizeof(long long) * SMn);
+            h->off_dual = take(sizeof(double) * 3 * SMn * kDualPerNode);
+            h->off_res = take(sizeof(double) * (size_t)c.S * kResPerSlice);
+            h->off_stats = take(sizeof(double) * (size_t)kStatsCap * c.S * DADMM_NSTAT);
+            h->off_status = take(sizeof(int) * 4);
+            h->ws_bytes = off + 256;
+            TOMO_CUDA(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+            TOMO_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+            TOMO_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+        } catch (...) {
+            free_dadmm(h);
+            throw;
+        }
+        *out = reinterpret_cast<dadmm_t>(h);
+    });
+}
+
+tomo_status dadmm_destroy(dadmm_t hh) {
+    return guard([&] {
+        if (hh) free_dadmm(as_dadmm(hh));
+    });
+}
+
+int dadmm_ring_depth(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->D : 0; }
+
+size_t dadmm_state_size(dadmm_t hh) {
+    if (!hh) return 0;
+    const Dadmm& h = *reinterpret_cast<Dadmm*>(hh);
+    const size_t n = (size_t)h.N * h.N;
+    return sizeof(float) * (2 * (size_t)h.S * h.M * n + (size_t)h.S * n + (size_t)h.D * 3 * h.S * n) + sizeof(int32_t);
+}
+
+size_t dadmm_workspace_size(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->ws_bytes : 0; }
+
+tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t stream) {
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        check_device(*h.g);
+        TOMO_REQUIRE(st && st->u && st->lam && st->xseg && st->hist && st->iter, "state pointers must be non-NULL");
+        const size_t n = (size_t)h.N * h.N;
+        cudaStream_t s = (cudaStream_t)stream;
+        TOMO_CUDA(cudaMemsetAsync(st->u, 0, sizeof(float) * h.S * h.M * n, s));
+        TOMO_CUDA(cudaMemsetAsync(st->lam, 0, sizeof(float) * h.S * h.M * n, s));
+        TOMO_CUDA(cudaMemsetAsync(st->xseg, 0, sizeof(float) * h.S * n, s));
+        TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * (size_t)h.D * 3 * h.S * n, s));
+        TOMO_CUDA(cudaMemsetAsync(st->iter, 0, sizeof(int32_t), s));
+    });
+}
+
+tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters, void* workspace,
+                       size_t workspace_bytes, double* stats, tomo_stream_t stream) {
+    tomo_status numeric = TOMO_OK;
+    tomo_status rc = guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        check_device(*h.g);
+        TOMO_REQUIRE(st && st->u && st->lam && st->xseg && st->hist && st->iter, "state pointers must be non-NULL");
+        TOMO_REQUIRE(sino != nullptr, "sino is NULL");
+        TOMO_REQUIRE(n_iters >= 0, "n_iters must be >= 0");
+        TOMO_REQUIRE(((uintptr_t)st->u | (uintptr_t)st->lam | (uintptr_t)st->xseg | (uintptr_t)st->hist) % 16 == 0,
+                     "state arrays must be 16-byte aligned");
+        TOMO_REQUIRE(workspace != nullptr && workspace_bytes >= h.ws_bytes,
+                     "workspace too small: need " + std::to_string(h.ws_bytes) + " bytes");
+        if (n_iters == 0) return;
+        cudaStream_t user = (cudaStream_t)stream;
+        const WsPtrs w = ws_ptrs(h, workspace);
+        int k0 = 0;
+        if (stats) {
+            TOMO_CUDA(cudaMemcpyAsync(&k0, st->iter, sizeof(int), cudaMemcpyDeviceToHost, user));
+            TOMO_CUDA(cudaStreamSynchronize(user));
+            TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), user));
+        }
+        if (h.mode == DADMM_MODE_BATCHED) {
+            const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
+                                                  w.resid};
+            if (!h.gexec || key != h.gkey) {
+                if (h.gexec) {
+                    TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
+                    h.gexec = nullptr;
+                }
+                cudaGraph_t graph = nullptr;
+                TOMO_CUDA(cudaStreamBeginCapture(h.own, cudaStreamCaptureModeThreadLocal));
+                try {
+                    enqueue_iteration(h, *st, sino, w, h.own);
+                } catch (...) {
+                    cudaStreamEndCapture(h.own, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                TOMO_CUDA(cudaStreamEndCapture(h.own, &graph));
+                cudaError_t e = cudaGraphInstantiate(&h.gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                TOMO_CUDA(e);
+                h.gkey = key;
+            }
+            TOMO_CUDA(cudaEventRecord(h.ev_in, user));
+            TOMO_CUDA(cudaStreamWaitEvent(h.own, h.ev_in, 0));
+            for (int it = 0; it < n_iters; ++it) TOMO_CUDA(cudaGraphLaunch(h.gexec, h.own));
+            TOMO_CUDA(cudaEventRecord(h.ev_out, h.own));
+            TOMO_CUDA(cudaStreamWaitEvent(user, h.ev_out, 0));
+        } else {
+            for (int it = 0; it < n_iters; ++it) enqueue_iteration(h, *st, sino, w, user);
+        }
+        if (stats) {
+            const int keep = std::min(n_iters, kStatsCap);
+            std::vector<double> ring((size_t)kStatsCap * h.S * DADMM_NSTAT);
+            int status = 0;
+            TOMO_CUDA(cudaMemcpyAsync(ring.data(), w.stats, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, user));
+            TOMO_CUDA(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, user));
+            TOMO_CUDA(cudaStreamSynchronize(user));
+            const size_t per = (size_t)h.S * DADMM_NSTAT;
+            for (int it = 0; it < n_iters; ++it) {
+                if (it < n_iters - keep) {  // overwritten in the ring: report NaN
+                    for (size_t q = 0; q < per; ++q) stats[(size_t)it * per + q] = NAN;
+                    continue;
+                }
+                const int kk = k0 + it;
+                std::memcpy(stats + (size_t)it * per, ring.data() + (size_t)(kk % kStatsCap) * per, sizeof(double) * per);
+            }
+            if (status & 1) fail(TOMO_ERR_CUDA, "projector staging extent exceeded (internal error)");
+            if (status & 2) numeric = TOMO_ERR_NUMERIC;
+        }
+    });
+    if (rc == TOMO_OK && numeric != TOMO_OK) {
+        set_last_error("non-finite statistics");
+        return numeric;
+    }
+    return rc;
+}
+
+tomo_status dadmm_set_profiling(dadmm_t hh, int enable) {
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        check_device(*h.g);
+        if (enable && h.pev.empty()) {
+            h.pev.resize(h.num_phases() + 1);
+            for (auto& e : h.pev) TOMO_CUDA(cudaEventCreate(&e));
+        }
+        h.profiling = enable != 0;
+        if (h.gexec) {  // the next step re-captures with or without the event nodes
+            TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
+            h.gexec = nullptr;
+        }
+    });
+}
+
+int dadmm_num_phases(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->num_phases() : 0; }
+
+tomo_status dadmm_phase_times(dadmm_t hh, float* ms, int n) {
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        TOMO_REQUIRE(h.profiling && !h.pev.empty(), "profiling is not enabled");
+        TOMO_REQUIRE(ms != nullptr, "ms is NULL");
+        TOMO_CUDA(cudaEventSynchronize(h.pev.back()));
+        const int np = std::min(n, h.num_phases());
+        for (int i = 0; i < np; ++i) TOMO_CUDA(cudaEventElapsedTime(ms + i, h.pev[i], h.pev[i + 1]));
+    });
+}
+
+tomo_status dadmm_home_view(dadmm_t hh, const dadmm_state* st, float* out, tomo_stream_t stream) {
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        check_device(*h.g);
+        TOMO_REQUIRE(st && st->hist && st->iter && out, "state and out must be non-NULL");
+        home_view_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(st->hist, st->iter, h.d_seg_of_row, h.d_home,
+                                                                  out, h.N, h.S, h.D);
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,886 @@
+// Discrete parallel-beam x-ray transform on GB300 (sm_103a):
+//   - the per-angle trig table in constant memory,
+//   - the ray-driven projector (image chunks staged in shared memory),
+//   - the pixel-driven matched backprojector (sinogram windows staged in
+//     shared memory) with a plain epilogue and the fused Algorithm 2 u-step,
+//   - the C ABI of tomo_geometry_*, tomo_project, tomo_backproject,
+//     tomo_opnorm_sq.
+//
+// The operator (Sec. 2.1, Eq. 2-4): P[(a,b),(i,j)] is the length of the line
+// x cos(theta_a) + y sin(theta_a) = t_b inside pixel (i, j). Projected onto
+// the ray normal, a unit square is a trapezoid of area 1: with c = cos,
+// s = sin, tau = t_b - (x_j c + y_i s),
+//   T(tau) = h * sat(0.5 + gamma (w_mid - |tau|)),
+//   h = 1/max(|c|,|s|), gamma = 1/min(|c|,|s|), w_mid = max(|c|,|s|)/2.
+// For axis-aligned rays (min = 0) gamma is capped at 2^20; every quantity is
+// then an exact half-integer, so the formula yields the exact box values
+// {1, 1/2, 0} with 1/2 for a ray on a pixel edge.
+//
+// Both kernels evaluate that same formula, so the backprojector is the exact
+// transpose of the projector up to FP32 rounding. Positions are carried in
+// 2^-40 fixed point (int64) from the block origin, so that FP32 only ever
+// holds offsets below 64 pixels: the weight error stays at ~1e-6 even at
+// N = 2048 and for the steep ramps of near-axis angles.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+// ------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+void clear_last_error() { g_last_error.clear(); }
+void fail(tomo_status code, const std::string& msg) { throw Error{code, msg}; }
+
+// ------------------------------------------------------------------
+// constant trig pool: (cos, sin) of every angle of every live geometry
+// ------------------------------------------------------------------
+__constant__ double2 c_trig[TOMO_MAX_CONST_ANGLES];
+
+namespace {
+struct ConstPool {
+    std::mutex mu;
+    // per device: occupied slots
+    std::vector<std::vector<char>> used;
+};
+ConstPool& pool() {
+    static ConstPool p;
+    return p;
+}
+
+int pool_alloc(int device, int count) {
+    ConstPool& P = pool();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if ((int)P.used.size() <= device) P.used.resize(device + 1);
+    auto& u = P.used[device];
+    if (u.empty()) u.assign(TOMO_MAX_CONST_ANGLES, 0);
+    int run = 0;
+    for (int i = 0; i < TOMO_MAX_CONST_ANGLES; ++i) {
+        run = u[i] ? 0 : run + 1;
+        if (run == count) {
+            int first = i - count + 1;
+            for (int k = first; k <= i; ++k) u[k] = 1;
+            return first;
+        }
+    }
+    return -1;
+}
+
+void pool_free(int device, int first, int count) {
+    ConstPool& P = pool();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (first < 0 || device >= (int)P.used.size()) return;
+    for (int k = first; k < first + count; ++k) P.used[device][k] = 0;
+}
+}  // namespace
+
+Geometry* as_geometry(tomo_geometry_t g) {
+    TOMO_REQUIRE(g != nullptr, "geometry handle is NULL");
+    return reinterpret_cast<Geometry*>(g);
+}
+
+void check_device(const Geometry& g) {
+    int dev = -1;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    TOMO_REQUIRE(dev == g.device, "geometry was created on device " + std::to_string(g.device) +
+                                      " but the current device is " + std::to_string(dev));
+}
+
+// ------------------------------------------------------------------
+// per-angle parameters, derived in FP64 from the constant table
+// ------------------------------------------------------------------
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic rounds x to an integer
+constexpr int kMagicI = 0x4B400000;    // bit pattern of kMagic
+constexpr float kGammaCap = 1048576.0f;  // 2^20
+
+struct ProjAngle {
+    long long Db, Dm, K0;  // minor coordinate of ray b at major index m: b Db + m Dm + K0 (2^-40)
+    float dm;              // Dm in FP32, for stepping inside a chunk
+    float kappa;           // |major| / |minor|: slope of the weight in minor-index units
+    float h;               // 1 / |major|
+    int colmaj;            // 0: image rows are the major axis; 1: columns
+};
+
+__device__ __forceinline__ ProjAngle proj_angle(int N, int B, double2 cs) {
+    const double c = cs.x, s = cs.y, hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
+    const double ac = fabs(c), as = fabs(s);
+    ProjAngle r;
+    double db, dm, k0, maj, mnr;
+    if (ac >= as) {  // ray crosses each row once: column coordinate per row
+        db = 1.0 / c;
+        dm = s / c;
+        k0 = -hB / c - (hN * s) / c + hN;
+        maj = ac;
+        mnr = as;
+        r.colmaj = 0;
+    } else {  // ray crosses each column once: row coordinate per column
+        db = -1.0 / s;
+        dm = c / s;
+        k0 = hN + hB / s - (hN * c) / s;
+        maj = as;
+        mnr = ac;
+        r.colmaj = 1;
+    }
+    r.Db = __double2ll_rn(db * kFix);
+    r.Dm = __double2ll_rn(dm * kFix);
+    r.K0 = __double2ll_rn(k0 * kFix);
+    r.dm = (float)dm;
+    r.kappa = mnr > 0.0 ? (float)(maj / mnr) : kGammaCap;
+    r.h = (float)(1.0 / maj);
+    return r;
+}
+
+struct BpAngle {
+    long long C, S, K;  // bin coordinate of pixel (i, j): j C - i S + K (2^-40)
+    float c, s;         // FP32 steps for the pixels of one thread
+    float gam, alpha;   // weight = sat(alpha -+ gam e) in bin units
+    float h;            // folded into the staged sinogram values
+    int w0;             // first staged bin of this tile
+    const float* row;   // sinogram line
+};
+
+__device__ __forceinline__ void bp_angle(BpAngle& r, int N, int B, double2 cs) {
+    const double c = cs.x, s = cs.y, hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
+    const double ac = fabs(c), as = fabs(s);
+    const double mx = fmax(ac, as), mn = fmin(ac, as);
+    r.C = __double2ll_rn(c * kFix);
+    r.S = __double2ll_rn(s * kFix);
+    r.K = __double2ll_rn((hB - hN * c + hN * s) * kFix);
+    r.c = (float)c;
+    r.s = (float)s;
+    const double gam = mn > 0.0 ? 1.0 / mn : (double)kGammaCap;
+    r.gam = (float)gam;
+    r.alpha = (float)(0.5 + gam * (0.5 * mx - 0.5));
+    r.h = (float)(1.0 / mx);
+}
+
+__device__ __forceinline__ float frac40_to_float(long long p) {
+    // top 23 bits of the 40-bit fraction as a float in [0, 1)
+    return __int_as_float(0x3F800000 | (int)((p >> 17) & 0x7FFFFF)) - 1.0f;
+}
+
+// ------------------------------------------------------------------
+// projector
+// ------------------------------------------------------------------
+__global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams p) {
+    extern __shared__ float tile[];  // [kProjRows][kProjPitch]
+    __shared__ ProjAngle sa[kProjMaxNa];
+    __shared__ int s_item, s_q0, s_w;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = p.N, B = p.B;
+    const size_t n = (size_t)N * N;
+
+    for (int pass = 0;; ++pass) {
+        int it;
+        if (p.counter) {
+            if (tid == 0) s_item = atomicAdd(p.counter, 1);
+            __syncthreads();
+            it = s_item;
+        } else {
+            it = pass == 0 ? (int)blockIdx.x : p.n_items;
+        }
+        if (it >= p.n_items) break;
+        const ProjItem item = p.items[it];
+        if (tid < item.na) sa[tid] = proj_angle(N, B, c_trig[p.const_off + p.angs[item.ang0 + tid].angle]);
+        __syncthreads();
+
+        const int na = item.na, wb = kProjThreads / na;
+        const int slot = tid / wb;
+        const int b = item.b0 + tid % wb;
+        const int blast = min(item.b0 + wb - 1, B - 1);
+        const int bc = min(b, blast);  // rays past the last bin shadow it (their output is dropped)
+        const ProjAngle A = sa[slot];
+        const int colmaj = sa[0].colmaj;
+        const float* img = p.img + (size_t)item.img * n;
+        float total = 0.f;
+
+        for (int ch = 0; ch < item.nchunks; ++ch) {
+            const int m0 = item.m_lo + ch * kProjRows;
+            if (warp == 0) {  // staged minor range: extremes over the item's corner rays
+                long long lo = LLONG_MAX, hi = LLONG_MIN;
+                if (lane < 4 * na) {
+                    const ProjAngle& C = sa[lane >> 2];
+                    const int bb = (lane & 1) ? blast : item.b0;
+                    const int mm = (lane & 2) ? m0 + kProjRows - 1 : m0;
+                    lo = hi = (long long)bb * C.Db + (long long)mm * C.Dm + C.K0;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if (lane == 0) {
+                    const int q0 = (int)(lo >> 40) - 2;
+                    s_q0 = q0;
+                    s_w = (int)(hi >> 40) + 3 - q0;
+                }
+            }
+            __syncthreads();  // previous chunk fully consumed; s_q0/s_w visible
+            const int q0 = s_q0, w = s_w;
+            if (w > kProjWMax) {  // unreachable: the host bounds every item's extent
+                if (tid == 0 && p.status) atomicOr(p.status, 1);
+                __syncthreads();  // every thread has read s_q0 / s_w
+                continue;
+            }
+            if (!colmaj) {
+                for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
+                    const int row = m0 + r;
+                    const bool rok = row >= 0 && row < N;
+                    const float* src = img + (size_t)(rok ? row : 0) * N;
+                    for (int q = lane; q < w; q += 32) {
+                        const int col = q0 + q;
+                        tile[r * kProjPitch + q] = (rok && col >= 0 && col < N) ? __ldg(src + col) : 0.f;
+                    }
+                }
+            } else {
+                const int col = m0 + lane;
+                const bool cok = col >= 0 && col < N;
+                for (int q = warp; q < w; q += kProjThreads / 32) {
+                    const int row = q0 + q;
+                    tile[lane * kProjPitch + q] =
+                        (cok && row >= 0 && row < N) ? __ldg(img + (size_t)row * N + col) : 0.f;
+                }
+            }
+            __syncthreads();
+
+            const long long pos = (long long)bc * A.Db + (long long)m0 * A.Dm + A.K0;
+            const int off = ((int)(pos >> 40) - q0) - kMagicI;
+            const float fm = frac40_to_float(pos) - 0.5f;
+            float acc = 0.f;
+#pragma unroll
+            for (int r = 0; r < kProjRows; ++r) {
+                const float pm = fmaf((float)r, A.dm, fm);  // ray centre - 1/2, minor units
+                const float q = pm + kMagic;                 // rint(pm) + kMagic
+                const float e = pm - (q - kMagic);           // in [-1/2, 1/2]
+                const float* t = tile + r * kProjPitch + (__float_as_int(q) + off);
+                const float u0 = t[0], u1 = t[1];
+                const float w0 = __saturatef(fmaf(-A.kappa, e, 0.5f));
+                const float w1 = __saturatef(fmaf(A.kappa, e, 0.5f));
+                acc = fmaf(w0, u0, acc);
+                acc = fmaf(w1, u1, acc);
+            }
+            total += acc;
+        }
+
+        if (b < B) {
+            const AngRow ar = p.angs[item.ang0 + slot];
+            const size_t o = ((size_t)item.outb + ar.row) * B + b;
+            float v = A.h * total;
+            if (p.sub) v -= __ldg(p.sub + o);
+            p.out[o] = v;
+        }
+        __syncthreads();  // sa / s_item reused by the next item
+    }
+}
+
+// ------------------------------------------------------------------
+// backprojector
+// ------------------------------------------------------------------
+enum { EPI_STORE = 0, EPI_USTEP = 1 };
+
+template <int EPI>
+__global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams p) {
+    __shared__ float2 win[kBpChunk][kBpWin];  // (v[b], v[b+1]) pairs, h folded in
+    __shared__ BpAngle sa[kBpChunk];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // 16 x 16 threads, each 4 (x) x 2 (y) pixels; a warp covers 32 x 8 pixels
+    const int tx = (lane & 7) + 8 * (warp & 1);
+    const int ty = (lane >> 3) + 4 * (warp >> 1);
+    const int N = p.N, B = p.B;
+    const size_t n = (size_t)N * N;
+
+    for (int pass = 0;; ++pass) {
+        int it;
+        if (p.counter) {
+            if (tid == 0) s_item = atomicAdd(p.counter, 1);
+            __syncthreads();
+            it = s_item;
+        } else {
+            it = pass == 0 ? (int)blockIdx.x : p.n_items;
+        }
+        if (it >= p.n_items) break;
+        const BpItem item = p.items[it];
+        const int x0 = item.tx * kBpTileX, y0 = item.ty * kBpTileY;
+        const int px = x0 + 4 * tx, py = y0 + 2 * ty;  // this thread's first pixel (column, row)
+        float acc[2][4];
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
+
+        for (int a0 = 0; a0 < item.na; a0 += kBpChunk) {
+            const int nac = min(kBpChunk, item.na - a0);
+            if (tid < nac) {
+                BpAngle& A = sa[tid];
+                const AngRow ar = p.angs[item.ang0 + a0 + tid];
+                bp_angle(A, N, B, c_trig[p.const_off + ar.angle]);
+                A.row = p.sino + ((size_t)item.sinb + ar.row) * B;
+                // lowest bin coordinate over the tile corners, minus a margin
+                long long lo = LLONG_MAX;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long j = x0 + ((k & 1) ? kBpTileX - 1 : 0);
+                    const long long i = y0 + ((k & 2) ? kBpTileY - 1 : 0);
+                    lo = min(lo, j * A.C - i * A.S + A.K);
+                }
+                A.w0 = (int)(lo >> 40) - 2;
+            }
+            __syncthreads();
+            for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
+                const int a = e / kBpWin, k = e - a * kBpWin;
+                const BpAngle& A = sa[a];
+                const int b = A.w0 + k;
+                const float v0 = (b >= 0 && b < B) ? __ldg(A.row + b) : 0.f;
+                const float v1 = (b + 1 >= 0 && b + 1 < B) ? __ldg(A.row + b + 1) : 0.f;
+                win[a][k] = make_float2(A.h * v0, A.h * v1);
+            }
+            __syncthreads();
+            for (int a = 0; a < nac; ++a) {
+                const BpAngle& A = sa[a];
+                const long long pfx = (long long)px * A.C - (long long)py * A.S + A.K;
+                const int off = ((int)(pfx >> 40) - A.w0) - kMagicI;
+                const float fm = frac40_to_float(pfx) - 0.5f;
+                const float2* wa = win[a];
+                const float c = A.c, s = A.s, gam = A.gam, alpha = A.alpha;
+#pragma unroll
+                for (int ky = 0; ky < 2; ++ky) {
+                    const float rowm = fmaf(-(float)ky, s, fm);
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx) {
+                        const float pm = fmaf((float)kx, c, rowm);  // bin coordinate - 1/2
+                        const float q = pm + kMagic;
+                        const float e = pm - (q - kMagic);
+                        const float2 r = wa[__float_as_int(q) + off];
+                        const float w0 = __saturatef(fmaf(-gam, e, alpha));
+                        const float w1 = __saturatef(fmaf(gam, e, alpha));
+                        acc[ky][kx] = fmaf(w0, r.x, acc[ky][kx]);
+                        acc[ky][kx] = fmaf(w1, r.y, acc[ky][kx]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        if (EPI == EPI_STORE) {
+            float* img = p.img + (size_t)item.img * n;
+#pragma unroll
+            for (int ky = 0; ky < 2; ++ky) {
+                const int row = py + ky;
+                if (row >= N) continue;
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) {
+                    const int col = px + kx;
+                    if (col >= N) continue;
+                    float* o = img + (size_t)row * N + col;
+                    *o = (p.beta != 0.f ? *o : 0.f) + acc[ky][kx];
+                }
+            }
+        } else {
+            // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
+            const BpView& V = p.view;
+            const int k = *V.iter;
+            const float eta = V.eta1[item.node];
+            float* u = V.u + (size_t)item.img * n;
+            const float* lam = V.lam + (size_t)item.img * n;
+#pragma unroll
+            for (int ky = 0; ky < 2; ++ky) {
+                const int row = py + ky;
+                if (row >= N) continue;
+                const int seg = V.seg_of_row[row];
+                const int mi = item.node * V.M + seg;
+                const int j = k - V.lag[mi];
+                const float* xv = nullptr;
+                if (j >= 1)
+                    xv = V.hist + ((((size_t)(j % V.D) * 3 + V.kind[mi]) * V.S + item.slice) * n) +
+                         (size_t)row * N;
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) {
+                    const int col = px + kx;
+                    if (col >= N) continue;
+                    const size_t o = (size_t)row * N + col;
+                    const float uo = u[o];
+                    const float x = xv ? xv[col] : 0.f;
+                    const float g = acc[ky][kx] + V.rho * (uo - x) + lam[o];
+                    u[o] = uo - eta * g;
+                }
+            }
+        }
+    }
+}
+
+static size_t proj_smem() { return sizeof(float) * kProjRows * kProjPitch; }
+
+void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
+    if (p.n_items == 0) return;
+    static bool attr = false;
+    if (!attr) {
+        TOMO_CUDA(cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)proj_smem()));
+        attr = true;
+    }
+    project_kernel<<<grid, kProjThreads, proj_smem(), st>>>(p);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st) {
+    if (p.n_items == 0) return;
+    backproject_kernel<EPI_STORE><<<grid, kBpThreads, 0, st>>>(p);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st) {
+    if (p.n_items == 0) return;
+    backproject_kernel<EPI_USTEP><<<grid, kBpThreads, 0, st>>>(p);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    TOMO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+int persistent_grid_project() {
+    int per_sm = 0;
+    TOMO_CUDA(cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)proj_smem()));
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel, kProjThreads,
+                                                            proj_smem()));
+    return sm_count() * (per_sm > 0 ? per_sm : 1);
+}
+
+int persistent_grid_backproject(bool ustep) {
+    int per_sm = 0;
+    if (ustep)
+        TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_USTEP>,
+                                                                kBpThreads, 0));
+    else
+        TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_STORE>,
+                                                                kBpThreads, 0));
+    return sm_count() * (per_sm > 0 ? per_sm : 1);
+}
+
+// ------------------------------------------------------------------
+// host work-list builders
+// ------------------------------------------------------------------
+namespace {
+struct HostProj {  // FP64 mirror of ProjAngle (positions, not fixed point)
+    double db, dm, k0;
+    bool colmaj;
+};
+HostProj host_proj(const Geometry& g, int a) {
+    const double c = g.c[a], s = g.s[a], hN = 0.5 * (g.N - 1), hB = 0.5 * (g.B - 1);
+    HostProj r;
+    if (rows_major(c, s)) {
+        r.db = 1.0 / c;
+        r.dm = s / c;
+        r.k0 = -hB / c - (hN * s) / c + hN;
+        r.colmaj = false;
+    } else {
+        r.db = -1.0 / s;
+        r.dm = c / s;
+        r.k0 = hN + hB / s - (hN * c) / s;
+        r.colmaj = true;
+    }
+    return r;
+}
+
+// major-index interval [lo, hi] on which any ray b0..b1 of angle A lies
+// within the image's minor range (conservative by one pixel)
+void major_range(const HostProj& A, int b0, int b1, int N, int& lo, int& hi) {
+    const double plo = std::min(b0 * A.db, b1 * A.db) + A.k0;
+    const double phi = std::max(b0 * A.db, b1 * A.db) + A.k0;
+    const double lim_lo = -2.0, lim_hi = N + 1.0;
+    // need m dm + phi >= lim_lo and m dm + plo <= lim_hi
+    double a = 0.0, b = N - 1.0;
+    if (A.dm > 0) {
+        a = std::max(a, (lim_lo - phi) / A.dm);
+        b = std::min(b, (lim_hi - plo) / A.dm);
+    } else if (A.dm < 0) {
+        a = std::max(a, (lim_hi - plo) / A.dm);
+        b = std::min(b, (lim_lo - phi) / A.dm);
+    } else if (phi < lim_lo || plo > lim_hi) {
+        b = -1.0;
+    }
+    lo = (int)std::floor(a) - 1;
+    hi = (int)std::ceil(b) + 1;
+    lo = std::max(lo, 0);
+    hi = std::min(hi, N - 1);
+}
+
+// upper bound of the staged extent of one item chunk, mirroring the kernel
+int chunk_extent(const std::vector<HostProj>& As, int b0, int b1, int m0) {
+    double lo = 1e300, hi = -1e300;
+    for (const HostProj& A : As)
+        for (int bb : {b0, b1})
+            for (int mm : {m0, m0 + kProjRows - 1}) {
+                const double v = bb * A.db + mm * A.dm + A.k0;
+                lo = std::min(lo, v);
+                hi = std::max(hi, v);
+            }
+    const int q0 = (int)std::floor(lo) - 2;
+    return (int)std::floor(hi) + 3 - q0 + 2;  // +2 slack over the kernel's fixed-point value
+}
+}  // namespace
+
+void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int ang_begin,
+                      int ang_count, int img, int outb, std::vector<ProjItem>& out) {
+    const int end = ang_begin + ang_count;
+    int i = ang_begin;
+    while (i < end) {
+        int na = kProjMaxNa;
+        for (; na > 1; na /= 2) {
+            if (i + na > end) continue;
+            const bool cm = rows_major(g.c[angs[i].angle], g.s[angs[i].angle]);
+            bool same = true;
+            for (int k = 1; k < na; ++k)
+                same &= rows_major(g.c[angs[i + k].angle], g.s[angs[i + k].angle]) == cm;
+            if (!same) continue;
+            // extent check over every bin run and chunk
+            std::vector<HostProj> As;
+            for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
+            const int wb = kProjThreads / na;
+            bool ok = true;
+            for (int b0 = 0; b0 < g.B && ok; b0 += wb) {
+                const int b1 = std::min(b0 + wb - 1, g.B - 1);
+                int lo = g.N, hi = -1;
+                for (const HostProj& A : As) {
+                    int l, h;
+                    major_range(A, b0, b1, g.N, l, h);
+                    if (h >= l) {
+                        lo = std::min(lo, l);
+                        hi = std::max(hi, h);
+                    }
+                }
+                for (int m0 = lo; m0 <= hi && ok; m0 += kProjRows)
+                    ok = chunk_extent(As, b0, b1, m0) <= kProjWMax;
+            }
+            if (ok) break;
+        }
+        std::vector<HostProj> As;
+        for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
+        const int wb = kProjThreads / na;
+        for (int b0 = 0; b0 < g.B; b0 += wb) {
+            const int b1 = std::min(b0 + wb - 1, g.B - 1);
+            int lo = g.N, hi = -1;
+            for (const HostProj& A : As) {
+                int l, h;
+                major_range(A, b0, b1, g.N, l, h);
+                if (h >= l) {
+                    lo = std::min(lo, l);
+                    hi = std::max(hi, h);
+                }
+            }
+            ProjItem it{};
+            it.img = img;
+            it.outb = outb;
+            it.ang0 = i;
+            it.na = na;
+            it.b0 = b0;
+            it.m_lo = hi >= lo ? lo : 0;
+            it.nchunks = hi >= lo ? ceil_div(hi - lo + 1, kProjRows) : 0;
+            out.push_back(it);
+        }
+        i += na;
+    }
+}
+
+void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb, int node,
+                    int slice, std::vector<BpItem>& out) {
+    const int ntx = ceil_div(g.N, kBpTileX), nty = ceil_div(g.N, kBpTileY);
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            BpItem it{};
+            it.img = img;
+            it.sinb = sinb;
+            it.tx = tx;
+            it.ty = ty;
+            it.ang0 = ang_begin;
+            it.na = ang_count;
+            it.node = node;
+            it.slice = slice;
+            out.push_back(it);
+        }
+}
+
+// ------------------------------------------------------------------
+// opnorm helpers
+// ------------------------------------------------------------------
+__global__ void opnorm_init_kernel(float* x, size_t n, uint64_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        x[i] = (float)((z >> 40) * (1.0 / 16777216.0));
+    }
+}
+
+// out[0] = <x, y>, out[1] = <y, y> in FP64 (one block)
+__global__ void opnorm_dot_kernel(const float* x, const float* y, size_t n, double* out) {
+    __shared__ double s0[32], s1[32];
+    double a = 0.0, b = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += (double)x[i] * y[i];
+        b += (double)y[i] * y[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s0[threadIdx.x >> 5] = a;
+        s1[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ta += s0[w];
+            tb += s1[w];
+        }
+        out[0] = ta;
+        out[1] = tb;
+    }
+}
+
+__global__ void opnorm_scale_kernel(const float* y, float* x, size_t n, const double* dots) {
+    const float inv = (float)(1.0 / sqrt(dots[1]));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = y[i] * inv;
+}
+
+}  // namespace tomo
+
+using namespace tomo;
+
+// ------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------
+extern "C" {
+
+const char* tomo_last_error(void) { return tomo::g_last_error.c_str(); }
+
+int tomo_version(void) { return 100; }
+
+tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* angles_rad,
+                                 tomo_geometry_t* out) {
+    return guard([&] {
+        TOMO_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        TOMO_REQUIRE(N >= 1 && N <= 8192, "N must be in [1, 8192]");
+        TOMO_REQUIRE(n_bins >= 1 && n_bins <= 16384, "n_bins must be in [1, 16384]");
+        TOMO_REQUIRE(n_angles >= 1 && n_angles <= 4096, "n_angles must be in [1, 4096]");
+        auto* g = new Geometry();
+        g->N = N;
+        g->B = n_bins;
+        g->A = n_angles;
+        g->c.resize(n_angles);
+        g->s.resize(n_angles);
+        const double half_pi = 1.57079632679489661923;
+        std::vector<double2> cs(n_angles);
+        for (int a = 0; a < n_angles; ++a) {
+            const double th = angles_rad ? angles_rad[a] : a * (3.14159265358979323846 / n_angles);
+            if (!std::isfinite(th)) {
+                delete g;
+                fail(TOMO_ERR_INVALID_ARG, "angle " + std::to_string(a) + " is not finite");
+            }
+            const double k = std::floor(th / half_pi + 0.5);
+            double c, s;
+            if (std::fabs(th - k * half_pi) < 1e-12) {
+                const long m = (((long)k % 4) + 4) % 4;
+                c = m == 0 ? 1.0 : m == 2 ? -1.0 : 0.0;
+                s = m == 1 ? 1.0 : m == 3 ? -1.0 : 0.0;
+            } else {
+                c = std::cos(th);
+                s = std::sin(th);
+            }
+            g->c[a] = c;
+            g->s[a] = s;
+            cs[a] = make_double2(c, s);
+        }
+        cudaError_t e = cudaGetDevice(&g->device);
+        if (e != cudaSuccess) {
+            delete g;
+            fail(TOMO_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        }
+        g->const_off = pool_alloc(g->device, n_angles);
+        if (g->const_off < 0) {
+            delete g;
+            fail(TOMO_ERR_WORKSPACE, "constant trig pool exhausted (" +
+                                         std::to_string(TOMO_MAX_CONST_ANGLES) +
+                                         " angles shared by all live geometries)");
+        }
+        e = cudaMemcpyToSymbol(c_trig, cs.data(), sizeof(double2) * n_angles,
+                               sizeof(double2) * g->const_off, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            pool_free(g->device, g->const_off, n_angles);
+            delete g;
+            fail(TOMO_ERR_CUDA, std::string("cudaMemcpyToSymbol: ") + cudaGetErrorString(e));
+        }
+        *out = reinterpret_cast<tomo_geometry_t>(g);
+    });
+}
+
+tomo_status tomo_geometry_destroy(tomo_geometry_t gh) {
+    return guard([&] {
+        if (!gh) return;
+        Geometry* g = as_geometry(gh);
+        for (auto& s : g->cache) {
+            cudaFree(s.d_angs);
+            cudaFree(s.d_pitems);
+            cudaFree(s.d_bitems);
+        }
+        pool_free(g->device, g->const_off, g->A);
+        delete g;
+    });
+}
+
+}  // extern "C"
+
+namespace tomo {
+// cached work lists of a standalone selection (angle list + batch)
+static Geometry::Sel& selection(Geometry& g, const int32_t* angle_idx, int n_sel, int batch) {
+    std::vector<int32_t> key(n_sel);
+    for (int q = 0; q < n_sel; ++q) {
+        const int a = angle_idx ? angle_idx[q] : q;
+        TOMO_REQUIRE(a >= 0 && a < g.A, "angle index " + std::to_string(a) + " out of range");
+        key[q] = a;
+    }
+    std::lock_guard<std::mutex> lk(g.mu);
+    for (auto& s : g.cache)
+        if (s.batch == batch && s.key == key) return s;
+    Geometry::Sel s;
+    s.key = key;
+    s.batch = batch;
+    std::vector<AngRow> angs(n_sel);
+    for (int q = 0; q < n_sel; ++q) angs[q] = AngRow{key[q], q};
+    std::vector<ProjItem> pi;
+    std::vector<BpItem> bi;
+    for (int k = 0; k < batch; ++k) {
+        build_proj_items(g, angs, 0, n_sel, k, k * n_sel, pi);
+        build_bp_items(g, 0, n_sel, k, k * n_sel, 0, 0, bi);
+    }
+    s.d_angs = device_upload(angs);
+    s.d_pitems = device_upload(pi);
+    s.n_pitems = (int)pi.size();
+    s.d_bitems = device_upload(bi);
+    s.n_bitems = (int)bi.size();
+    if (g.cache.size() >= 16) {  // keep the cache small
+        cudaFree(g.cache.front().d_angs);
+        cudaFree(g.cache.front().d_pitems);
+        cudaFree(g.cache.front().d_bitems);
+        g.cache.erase(g.cache.begin());
+    }
+    g.cache.push_back(s);
+    return g.cache.back();
+}
+}  // namespace tomo
+
+extern "C" {
+
+tomo_status tomo_project(tomo_geometry_t gh, const float* img, float* sino, const int32_t* angle_idx,
+                         int n_sel, int batch, const float* subtract, tomo_stream_t stream) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        TOMO_REQUIRE(img && sino, "img and sino must be non-NULL");
+        TOMO_REQUIRE(batch >= 1, "batch must be >= 1");
+        TOMO_REQUIRE(n_sel >= 1 && n_sel <= 65536, "n_sel out of range");
+        TOMO_REQUIRE(angle_idx || n_sel == g->A, "angle_idx NULL requires n_sel == n_angles");
+        Geometry::Sel& s = selection(*g, angle_idx, n_sel, batch);
+        ProjParams p{};
+        p.img = img;
+        p.out = sino;
+        p.sub = subtract;
+        p.items = s.d_pitems;
+        p.angs = s.d_angs;
+        p.counter = nullptr;
+        p.status = nullptr;
+        p.n_items = s.n_pitems;
+        p.N = g->N;
+        p.B = g->B;
+        p.const_off = g->const_off;
+        launch_project(p, s.n_pitems, (cudaStream_t)stream);
+    });
+}
+
+tomo_status tomo_backproject(tomo_geometry_t gh, const float* sino, float* img, const int32_t* angle_idx,
+                             int n_sel, int batch, float beta, tomo_stream_t stream) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        TOMO_REQUIRE(img && sino, "img and sino must be non-NULL");
+        TOMO_REQUIRE(batch >= 1, "batch must be >= 1");
+        TOMO_REQUIRE(beta == 0.f || beta == 1.f, "beta must be 0 or 1");
+        TOMO_REQUIRE(n_sel >= 1 && n_sel <= 65536, "n_sel out of range");
+        TOMO_REQUIRE(angle_idx || n_sel == g->A, "angle_idx NULL requires n_sel == n_angles");
+        Geometry::Sel& s = selection(*g, angle_idx, n_sel, batch);
+        BpParams p{};
+        p.sino = sino;
+        p.img = img;
+        p.items = s.d_bitems;
+        p.angs = s.d_angs;
+        p.n_items = s.n_bitems;
+        p.N = g->N;
+        p.B = g->B;
+        p.const_off = g->const_off;
+        p.beta = beta;
+        launch_backproject_store(p, s.n_bitems, (cudaStream_t)stream);
+    });
+}
+
+size_t tomo_opnorm_workspace_size(tomo_geometry_t gh, int n_sel) {
+    if (!gh || n_sel < 1) return 0;
+    Geometry* g = reinterpret_cast<Geometry*>(gh);
+    const size_t n = (size_t)g->N * g->N;
+    return 256 + sizeof(float) * (2 * n + (size_t)n_sel * g->B) + 2 * sizeof(double) + 256;
+}
+
+tomo_status tomo_opnorm_sq(tomo_geometry_t gh, const int32_t* angle_idx, int n_sel, int iters,
+                           uint64_t seed, void* work, size_t work_bytes, double* out,
+                           tomo_stream_t stream) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        TOMO_REQUIRE(out && work, "out and work must be non-NULL");
+        TOMO_REQUIRE(iters >= 1, "iters must be >= 1");
+        TOMO_REQUIRE(work_bytes >= tomo_opnorm_workspace_size(gh, n_sel), "workspace too small");
+        const size_t n = (size_t)g->N * g->N;
+        char* w = (char*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+        float* x = (float*)w;
+        float* z = x + n;
+        float* y = z + n;
+        double* dots = (double*)(((uintptr_t)(y + (size_t)n_sel * g->B) + 15) & ~(uintptr_t)15);
+        cudaStream_t st = (cudaStream_t)stream;
+        opnorm_init_kernel<<<256, 256, 0, st>>>(x, n, seed);
+        TOMO_CUDA(cudaGetLastError());
+        // normalise the start vector
+        opnorm_dot_kernel<<<1, 1024, 0, st>>>(x, x, n, dots);
+        opnorm_scale_kernel<<<256, 256, 0, st>>>(x, x, n, dots);
+        for (int it = 0; it < iters; ++it) {
+            tomo_status rc = tomo_project(gh, x, y, angle_idx, n_sel, 1, nullptr, stream);
+            if (rc != TOMO_OK) fail(rc, tomo_last_error());
+            rc = tomo_backproject(gh, y, z, angle_idx, n_sel, 1, 0.f, stream);
+            if (rc != TOMO_OK) fail(rc, tomo_last_error());
+            opnorm_dot_kernel<<<1, 1024, 0, st>>>(x, z, n, dots);  // <x, P^T P x>, ||P^T P x||^2
+            if (it + 1 < iters) opnorm_scale_kernel<<<256, 256, 0, st>>>(z, x, n, dots);
+            TOMO_CUDA(cudaGetLastError());
+        }
+        double h[2];
+        TOMO_CUDA(cudaMemcpyAsync(h, dots, sizeof(h), cudaMemcpyDeviceToHost, st));
+        TOMO_CUDA(cudaStreamSynchronize(st));
+        *out = h[0];  // Rayleigh quotient at the unit vector x
+    });
+}
+
+}  // extern "C"

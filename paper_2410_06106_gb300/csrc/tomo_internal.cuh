@@ -1,0 +1,278 @@
+// Internal declarations shared by the translation units of libtomo.
+// Everything here is library-private; the public ABI is include/tomo.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tomo.h"
+
+namespace tomo {
+
+// ------------------------------------------------------------------
+// errors: every extern "C" entry point runs its body inside guard(), which
+// converts a thrown Error (or any exception) into a status code and records
+// the message for tomo_last_error().
+// ------------------------------------------------------------------
+struct Error {
+    tomo_status code;
+    std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+void clear_last_error();
+
+[[noreturn]] void fail(tomo_status code, const std::string& msg);
+
+#define TOMO_REQUIRE(cond, msg)                                                  \
+    do {                                                                         \
+        if (!(cond)) ::tomo::fail(TOMO_ERR_INVALID_ARG, std::string(msg));       \
+    } while (0)
+
+#define TOMO_CUDA(call)                                                          \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess)                                                   \
+            ::tomo::fail(TOMO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class F>
+tomo_status guard(F&& body) {
+    try {
+        clear_last_error();
+        body();
+        return TOMO_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        return e.code;
+    } catch (const std::exception& e) {
+        set_last_error(std::string("internal error: ") + e.what());
+        return TOMO_ERR_CUDA;
+    } catch (...) {
+        set_last_error("internal error");
+        return TOMO_ERR_CUDA;
+    }
+}
+
+// ------------------------------------------------------------------
+// geometry
+// ------------------------------------------------------------------
+
+// one (angle, sinogram row) pair of a selection: the angle indexes the
+// geometry's trig table, the row is where its sinogram line is read/written
+struct AngRow {
+    int angle;
+    int row;
+};
+
+// projector work item: na consecutive entries of an AngRow list that share
+// the major axis, a run of 256/na bins, the major-index range covering every
+// ray of the item, processed in chunks of kProjRows rows/columns
+struct ProjItem {
+    int img;      // image index (units of N*N floats)
+    int outb;     // output row base (added to AngRow::row)
+    int ang0;     // first AngRow entry
+    int na;       // angles in the item (1, 2 or 4)
+    int b0;       // first bin
+    int m_lo;     // first major index
+    int nchunks;  // chunks of kProjRows major indices
+    int pad;
+};
+
+// backprojector work item: one 64 x 32 pixel tile of one image, all the
+// angles of an AngRow run
+struct BpItem {
+    int img;   // image index (units of N*N floats); also the u/lambda index in dADMM
+    int sinb;  // sinogram row base (added to AngRow::row)
+    int tx, ty;
+    int ang0, na;
+    int node, slice;  // dADMM epilogue only
+};
+
+constexpr int kProjThreads = 256;
+constexpr int kProjRows = 32;   // rows per staged chunk
+constexpr int kProjWMax = 320;  // max staged minor extent
+constexpr int kProjPitch = kProjWMax + 1;
+constexpr int kProjMaxNa = 4;
+
+constexpr int kBpThreads = 256;
+constexpr int kBpTileX = 64, kBpTileY = 32;
+constexpr int kBpChunk = 32;  // angles staged per pass
+constexpr int kBpWin = 80;    // window pairs per angle
+
+constexpr double kFix = 1099511627776.0;  // 2^40, fixed-point scale of positions
+
+struct Geometry {
+    int N = 0, B = 0, A = 0;
+    int device = -1;
+    int const_off = -1;  // first slot of this geometry in the constant trig pool
+    std::vector<double> c, s;
+    // cached device work lists of standalone project/backproject calls
+    struct Sel {
+        std::vector<int32_t> key;
+        int batch = 0;
+        AngRow* d_angs = nullptr;
+        ProjItem* d_pitems = nullptr;
+        int n_pitems = 0;
+        BpItem* d_bitems = nullptr;
+        int n_bitems = 0;
+    };
+    std::vector<Sel> cache;
+    std::mutex mu;
+};
+
+// host: true when the rows of the image are the major (iteration) axis of
+// rays at this angle, i.e. |cos| >= |sin| (same test as the device)
+inline bool rows_major(double c, double s) { return std::abs(c) >= std::abs(s); }
+
+// host builders of work lists (operators.cu)
+void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int ang_begin,
+                      int ang_count, int img, int outb, std::vector<ProjItem>& out);
+void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb,
+                    int node, int slice, std::vector<BpItem>& out);
+
+// launch parameters
+struct ProjParams {
+    const float* img;
+    float* out;
+    const float* sub;  // may be null
+    const ProjItem* items;
+    const AngRow* angs;
+    int* counter;  // null: one block per item; else persistent work queue
+    int* status;   // device error word (may be null)
+    int n_items;
+    int N, B, const_off;
+};
+
+struct BpView {  // dADMM epilogue: where every node's view of x lives
+    const float* hist;        // [D][3][S][N][N]
+    const int32_t* iter;      // completed iterations k
+    const int8_t* lag;        // [M][M] (node, segment) -> relay lag
+    const int8_t* kind;       // [M][M] (node, segment) -> quantizer plane
+    const int32_t* seg_of_row;  // [N]
+    const float* eta1;        // [M]
+    float* u;                 // [S][M][N][N]
+    const float* lam;         // [S][M][N][N]
+    float rho;
+    int D, S, M;
+};
+
+struct BpParams {
+    const float* sino;
+    float* img;  // EPI_STORE target
+    const BpItem* items;
+    const AngRow* angs;
+    int* counter;
+    int* status;
+    int n_items;
+    int N, B, const_off;
+    float beta;
+    BpView view;
+};
+
+void launch_project(const ProjParams& p, int grid, cudaStream_t st);
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st);
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st);
+int persistent_grid_project();
+int persistent_grid_backproject(bool ustep);
+
+Geometry* as_geometry(tomo_geometry_t g);
+void check_device(const Geometry& g);
+
+// small helpers
+template <class T>
+T* device_upload(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    T* d = nullptr;
+    TOMO_CUDA(cudaMalloc(&d, sizeof(T) * v.size()));
+    TOMO_CUDA(cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return d;
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace tomo
+
+namespace tomo {
+
+// ------------------------------------------------------------------
+// codecs (codecs.cu)
+// ------------------------------------------------------------------
+constexpr int kKmThreads = 256;
+constexpr int kKmMaxK = 32;
+constexpr int kKmProbes = 64;
+
+// where the segment of (slice, owner) lives and where its messages go; built
+// by dadmm_create, read by the dADMM variants of the codec kernels
+struct SegTask {
+    int slice, owner;
+    int r0, r1;  // rows of the segment
+};
+
+struct DadmmCodec {
+    const float* xseg;    // [S][N][N]
+    float* hist;          // [D][3][S][N][N]
+    const int32_t* iter;  // completed iterations k (messages belong to k+1)
+    const SegTask* tasks;
+    int n_tasks;
+    int N, S, D;
+    uint64_t seed;
+    // JPEG only
+    const unsigned* lo_key;  // [S][M] order-preserving keys of the segment min / max
+    const unsigned* hi_key;
+    long long* nnz;          // [S][M]
+    int M;
+};
+
+void launch_kmeans_single(const float* in, long long n, int k, int iters, uint64_t key,
+                          uint8_t* codes, float* cent, float* deq, double* obj, cudaStream_t st);
+void launch_kmeans_dadmm(const DadmmCodec& p, int k, int iters, int task_begin, int task_count,
+                         cudaStream_t st);
+void launch_jpeg_single(const float* in, int rows, int cols, int quality, int16_t* coefs,
+                        float* lohi, float* deq, long long* nnz, cudaStream_t st);
+void launch_jpeg_dadmm(const DadmmCodec& p, int quality, int max_rows, int task_begin,
+                       int task_count, cudaStream_t st);
+size_t kmeans_smem(int kmax);
+void jpeg_quant_table(int quality, int32_t* qt);  // host, natural order
+
+// order-preserving map float -> unsigned (min/max with integer atomics)
+__host__ __device__ inline unsigned float_key(float f) {
+    unsigned u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    std::memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float key_float(unsigned k) {
+    unsigned u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// splitmix64 counter key of the K-means initialisation for (seed, slice, owner, iteration)
+__host__ __device__ inline uint64_t kmeans_key(uint64_t seed, int slice, int owner, int iter) {
+    const uint64_t ctr = ((uint64_t)(uint32_t)slice << 48) ^ ((uint64_t)(uint32_t)owner << 32) ^
+                         (uint64_t)(uint32_t)iter;
+    return mix64(seed ^ mix64(ctr + 0x9E3779B97F4A7C15ULL));
+}
+
+}  // namespace tomo

@@ -1,0 +1,101 @@
+"""GPU parity of the message quantizers (Sec. 2.7) against the oracle on the
+same FP32 inputs. K-means (Algorithm 5): codes identical except at rounding
+ties (<= 1e-4 of entries, each off by one level). JPEG: quantized
+coefficients and 8-bit levels identical except at rounding ties (<= 1e-4 of
+entries, each off by one)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_common import cuda, need_gpu, rel_l2
+from paper_2410_06106_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+def mixture(n, k, seed):
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-3, 3, k)
+    return (centres[rng.integers(0, k, n)] + rng.normal(0, 0.15, n)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,k,seed", [(8192, 16, 0), (65536, 32, 1), (16384, 16, 2), (1000, 3, 3),
+                                      (37, 8, 4), (5, 4, 5)])
+def test_kmeans_matches_oracle(n, k, seed):
+    need_gpu()
+    v = mixture(n, max(k // 2, 2), seed)
+    key = api.kmeans_key(99, 0, seed, 1)
+    assert key == O.kmeans_key(99, 0, seed, 1)
+    codes, cent, deq, obj = api.quant_kmeans(cuda(v), k, 10, key, objective=True)
+    oc, ocent, odeq, oobj = O.kmeans(v, k, 10, key)
+    codes = codes.cpu().numpy().astype(int)
+    diff = codes != oc
+    assert diff.mean() <= 1e-4 and np.all(np.abs(codes[diff] - oc[diff]) <= 1)
+    assert rel_l2(cent.cpu().numpy(), ocent) <= 1e-6
+    assert rel_l2(deq.cpu().numpy(), odeq) <= 1e-5
+    o = obj.cpu().numpy()
+    assert np.all(np.diff(o) <= 1e-9 * o[:-1] + 1e-12)
+    assert rel_l2(o, oobj) <= 1e-5
+
+
+def test_kmeans_constant_and_few_values_are_lossless():
+    need_gpu()
+    v = np.full(4096, 0.25, np.float32)
+    _, _, deq, _ = api.quant_kmeans(cuda(v), 16, 10, 7)
+    assert torch.equal(deq.cpu(), torch.as_tensor(v))
+    vals = np.array([-1.5, 0.0, 2.25], np.float32)
+    v = vals[np.arange(48) % 3]
+    _, _, deq, _ = api.quant_kmeans(cuda(v), 3, 10, 11)
+    assert torch.equal(deq.cpu(), torch.as_tensor(v))
+
+
+def smooth_segment(rows, cols, seed):
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:rows, 0:cols]
+    s = np.zeros((rows, cols))
+    for _ in range(6):
+        a, b, c = rng.uniform(0.01, 0.2, 3)
+        s += rng.uniform(-1, 1) * np.sin(a * x + b * y + c * 7)
+    return (s + 0.05 * rng.standard_normal((rows, cols))).astype(np.float32)
+
+
+@pytest.mark.parametrize("rows,cols,q", [(32, 256, 50), (32, 512, 50), (32, 2048, 75), (8, 8, 75),
+                                         (128, 1024, 10), (16, 64, 100)])
+def test_jpeg_matches_oracle(rows, cols, q):
+    need_gpu()
+    v = smooth_segment(rows, cols, rows + cols + q)
+    coefs, lohi, deq, nnz = api.quant_jpeg(cuda(v), q)
+    oc, olohi, odeq, onnz = O.jpeg(v, q)
+    c = coefs.cpu().numpy().astype(int)
+    diff = c != oc
+    assert diff.mean() <= 1e-4 and np.all(np.abs(c[diff] - oc[diff]) <= 1)
+    assert np.array_equal(lohi.cpu().numpy(), olohi)
+    step = (olohi[1] - olohi[0]) / 255.0
+    d = deq.cpu().numpy()
+    lev_diff = np.abs(d - odeq) > 0.5 * step
+    assert lev_diff.mean() <= 1e-4 and np.all(np.abs(d - odeq) <= 1.01 * step)
+    assert abs(int(nnz.item()) - onnz) <= max(2, int(1e-4 * c.size))
+
+
+def test_jpeg_exact_cases():
+    need_gpu()
+    lo, hi = np.float32(-0.3712), np.float32(2.9183)
+    rng = np.random.default_rng(2)
+    seg = np.where(rng.random((16, 24)) < 0.5, lo, hi).astype(np.float32)
+    seg[:8, :8] = lo
+    seg[8:, 16:] = hi
+    _, _, deq, _ = api.quant_jpeg(cuda(seg), 50)
+    d = deq.cpu().numpy()
+    assert np.array_equal(d[:8, :8], seg[:8, :8]) and np.array_equal(d[8:, 16:], seg[8:, 16:])
+    const = np.full((8, 16), np.float32(0.123), np.float32)
+    coefs, _, deq, nnz = api.quant_jpeg(cuda(const), 75)
+    assert torch.equal(deq.cpu(), torch.as_tensor(const)) and int(nnz.item()) == 0
+    for c in (0, 7, 100, 129, 255):  # constant blocks decide DC ties exactly like the oracle
+        seg = np.zeros((8, 16), np.float32)
+        seg[:, :8] = c
+        seg[0, 8], seg[1, 8] = 0.0, 255.0
+        coefs, _, deq, _ = api.quant_jpeg(cuda(seg), 50)
+        oc, _, odeq, _ = O.jpeg(seg, 50)
+        assert np.array_equal(coefs.cpu().numpy()[0], oc[0])
+        assert np.array_equal(deq.cpu().numpy()[:, :8], odeq[:, :8])

@@ -1,0 +1,142 @@
+"""GPU parity of the dADMM iteration (Algorithms 2-4, Eq. 15-18, 21-24)
+against the FP64 oracle.
+
+(i) state injection: the GPU's iterate k is loaded into the oracle, which runs
+one iteration; the GPU's iterate k+1 must match (u, lambda, x segments:
+relative L2 <= 1e-5; quantized messages: levels identical except at
+rounding ties);
+(ii) full trajectories: relative L2 of the reconstruction <= 1e-3 after the
+stated iterations;
+plus: the batched (persistent, graph-captured) and plain (per-node launch)
+forms are bit-identical, and a checkpoint resumes bit-identically."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_common import need_gpu, rel_l2
+from paper_2410_06106_gb300 import api, synth
+from problems import oracle_eta1, small_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_state(s):
+    return (s.u.cpu().numpy(), s.lam.cpu().numpy(), s.xseg.cpu().numpy(), s.hist.cpu().numpy(), s.k)
+
+
+def compare_states(g_next, o, prob, tol=1e-5, msg_frac=1e-4):
+    u, lam, xseg, hist, k = g_next
+    assert k == o.k
+    assert rel_l2(u, o.u) <= tol
+    assert rel_l2(lam, o.lam) <= tol * 10 + 1e-7 * 0  # lambda accumulates rho (u - x)
+    assert rel_l2(xseg, o.xseg) <= tol
+    slot = o.k % o.D
+    kinds = set(np.asarray(prob["home_q"]).tolist()) | set(
+        np.asarray(prob["edge_q"])[np.asarray(prob["adj"]) > 0].tolist())
+    for q in kinds:
+        a, b = hist[slot, q], o.hist[slot, q]
+        if q == 0:
+            assert rel_l2(a, b) <= tol
+        else:  # quantized planes: identical levels except at rounding ties
+            bad = np.abs(a - b) > 1e-4 * (np.abs(b).max() + 1e-30)
+            assert bad.mean() <= msg_frac, (q, bad.mean())
+
+
+@pytest.mark.parametrize("quant,graph,M", [("none", "ring", 4), ("kmeans", "ring", 4),
+                                          ("jpeg", "complete", 4), ("alternate", "ring", 8)])
+def test_state_injection_small(quant, graph, M):
+    need_gpu()
+    p = small_problem(N=64, A=48, B=91, M=M, graph=graph, quant=quant, part="blocks",
+                      noise=0.01, seed=M, km_k=16, jpeg_quality=50)
+    eta = oracle_eta1(p, iters=60)
+    s = api.DADMM(p, eta)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s.step(sino, 6)
+    before = gpu_state(s)
+    s.step(sino, 1)
+    after = gpu_state(s)
+    o = O.DADMM(p, eta)
+    o.load_state(*before)
+    o.iterate(p["sino"])
+    compare_states(after, o, p)
+
+
+@pytest.mark.parametrize("name", ["c2_kmeans", "c3_batch_jpeg"])
+def test_state_injection_full_config(name):
+    """one iteration of the full-size problem, injected after 3 GPU iterations"""
+    need_gpu()
+    p = synth.make_problem(name)
+    g = api.Geometry(p["geometry"]["N"], p["geometry"]["B"], p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    L = np.array([g.opnorm_sq(idx[ptr[m]:ptr[m + 1]], iters=30) for m in range(p["M"])])
+    eta = 1.0 / (L + p["rho"])  # any step works: both sides get the same input
+    s = api.DADMM(p, eta, geometry=g)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s.step(sino, 3)
+    before = gpu_state(s)
+    s.step(sino, 1)
+    after = gpu_state(s)
+    o = O.DADMM(p, eta)
+    o.load_state(*before)
+    o.iterate(p["sino"])
+    compare_states(after, o, p)
+
+
+def test_c1_trajectory_matches_oracle():
+    need_gpu()
+    p = synth.make_problem("c1_tiny")
+    eta = oracle_eta1(p, iters=60)
+    s = api.DADMM(p, eta)
+    st = s.step(torch.as_tensor(p["sino"]).cuda(), p["iters"])
+    o = O.DADMM(p, eta)
+    ost = [o.iterate(p["sino"]) for _ in range(p["iters"])]
+    x = s.home_view().cpu().numpy()
+    assert rel_l2(x, o.home_view()) <= 1e-3
+    ost = np.stack(ost)
+    assert rel_l2(st[:, :, 0], ost[:, :, 0]) <= 1e-3  # primal gap trajectory
+    assert np.all(st[:, :, 4] == ost[:, :, 4])        # bytes on the wire
+
+
+@pytest.mark.parametrize("quant", ["none", "alternate"])
+def test_batched_and_plain_forms_are_bit_identical(quant):
+    need_gpu()
+    p = small_problem(N=64, A=48, B=91, M=8, S=2, graph="ring", quant=quant, part="blocks", noise=0.01,
+                      km_k=16)
+    eta = oracle_eta1(p, iters=30)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    a = api.DADMM(p, eta, mode="batched")
+    b = api.DADMM(p, eta, mode="plain")
+    sa = a.step(sino, 5)
+    sb = b.step(sino, 5)
+    for name in ("u", "lam", "xseg", "hist"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    assert np.array_equal(sa, sb)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    need_gpu()
+    p = small_problem(N=64, A=48, B=91, M=4, graph="ring", quant="alternate", part="blocks", noise=0.01,
+                      km_k=16)
+    eta = oracle_eta1(p, iters=30)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s = api.DADMM(p, eta)
+    s.step(sino, 4)
+    ck = s.state_dict()
+    s.step(sino, 5)
+    x_a = s.home_view().clone()
+    s.load_state_dict(ck)
+    s.step(sino, 5)
+    assert torch.equal(s.home_view(), x_a)
+
+
+def test_stress_config_runs_and_reports():
+    """two iterations of the 8 x 2048^2, 64-node problem: finite statistics and
+    the byte count of the wire model"""
+    need_gpu()
+    p = synth.make_problem("c5_stress")
+    eta = np.full(p["M"], 1.0 / (0.9 * 28 * 2048 + 1.0))
+    s = api.DADMM(p, eta)
+    st = s.step(torch.as_tensor(p["sino"]).cuda(), 2)
+    assert np.all(np.isfinite(st))
+    assert np.all(st[:, :, 4] > 0)
