@@ -171,17 +171,27 @@ static void with_kmax(int k, F&& f) {
         f(std::integral_constant<int, 32>());
 }
 
+// dynamic shared-memory opt-in of the K-means kernels, once per process and
+// template instance, always before any stream capture
+template <int KMAX>
+static void ensure_km_attr() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        const int sm = (int)kmeans_smem(KMAX);
+        err = cudaFuncSetAttribute(kmeans_single_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(kmeans_dadmm_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    });
+    TOMO_CUDA(err);
+}
+
 void launch_kmeans_single(const float* in, long long n, int k, int iters, uint64_t key, uint8_t* codes,
                           float* cent, float* deq, double* obj, cudaStream_t st) {
     with_kmax(k, [&](auto KM) {
         constexpr int KMAX = decltype(KM)::value;
         const size_t sm = kmeans_smem(KMAX);
-        static bool attr = false;  // set once, before any stream capture
-        if (!attr) {
-            TOMO_CUDA(cudaFuncSetAttribute(kmeans_single_kernel<KMAX>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            attr = true;
-        }
+        ensure_km_attr<KMAX>();
         kmeans_single_kernel<KMAX><<<1, kKmThreads, sm, st>>>(in, n, k, iters, key, codes, cent, deq, obj);
         TOMO_CUDA(cudaGetLastError());
     });
@@ -193,12 +203,7 @@ void launch_kmeans_dadmm(const DadmmCodec& p, int k, int iters, int task_begin, 
     with_kmax(k, [&](auto KM) {
         constexpr int KMAX = decltype(KM)::value;
         const size_t sm = kmeans_smem(KMAX);
-        static bool attr = false;  // set once, before any stream capture
-        if (!attr) {
-            TOMO_CUDA(cudaFuncSetAttribute(kmeans_dadmm_kernel<KMAX>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            attr = true;
-        }
+        ensure_km_attr<KMAX>();
         kmeans_dadmm_kernel<KMAX><<<task_count, kKmThreads, sm, st>>>(p, k, iters, task_begin);
         TOMO_CUDA(cudaGetLastError());
     });
@@ -470,11 +475,7 @@ void launch_jpeg_dadmm(const DadmmCodec& p, int quality, int max_rows, int task_
 // everything that must not run while a stream is being captured
 void prepare_codecs(int km_k) {
     ensure_dct_table();
-    with_kmax(km_k < 1 ? 1 : km_k, [&](auto KM) {
-        constexpr int KMAX = decltype(KM)::value;
-        TOMO_CUDA(cudaFuncSetAttribute(kmeans_dadmm_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kmeans_smem(KMAX)));
-    });
+    with_kmax(km_k < 1 ? 1 : km_k, [&](auto KM) { ensure_km_attr<decltype(KM)::value>(); });
 }
 
 }  // namespace tomo

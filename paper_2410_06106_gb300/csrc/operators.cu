@@ -418,14 +418,19 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
 
 static size_t proj_smem() { return sizeof(float) * kProjRows * kProjPitch; }
 
+// the dynamic shared-memory opt-in, set once per process before any capture
+static void ensure_proj_attr() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
+    });
+    TOMO_CUDA(err);
+}
+
 void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
     if (p.n_items == 0) return;
-    static bool attr = false;
-    if (!attr) {
-        TOMO_CUDA(cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)proj_smem()));
-        attr = true;
-    }
+    ensure_proj_attr();
     project_kernel<<<grid, kProjThreads, proj_smem(), st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
@@ -451,8 +456,7 @@ static int sm_count() {
 
 int persistent_grid_project() {
     int per_sm = 0;
-    TOMO_CUDA(cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)proj_smem()));
+    ensure_proj_attr();
     TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel, kProjThreads,
                                                             proj_smem()));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
