@@ -136,15 +136,25 @@ class Geometry:
         self.N, self.B, self.A = int(N), int(B), int(A)
         self._theta = th
         h = C.c_void_p()
-        _check(lib().tomo_geometry_create(self.N, self.B, self.A,
-                                          th.ctypes.data_as(C.c_void_p) if th is not None else None,
-                                          C.byref(h)))
+        tp = th.ctypes.data_as(C.c_void_p) if th is not None else None
+        rc = lib().tomo_geometry_create(self.N, self.B, self.A, tp, C.byref(h))
+        if rc == -3:  # constant trig pool full: release unreachable geometries, retry once
+            import gc
+            gc.collect()
+            rc = lib().tomo_geometry_create(self.N, self.B, self.A, tp, C.byref(h))
+        _check(rc)
         self.handle = h
 
     def close(self):
         if getattr(self, "handle", None):
             lib().tomo_geometry_destroy(self.handle)
             self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

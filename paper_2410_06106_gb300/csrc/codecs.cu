@@ -228,8 +228,10 @@ void jpeg_quant_table(int quality, int32_t* qt) {
     }
 }
 
-// basis[p][x] = C(p)/2 cos((2x+1) p pi / 16), C(0) = 1/sqrt(2)
+// basis[p][x] = C(p)/2 cos((2x+1) p pi / 16), C(0) = 1/sqrt(2); FP32 for
+// the transforms, FP64 for re-deciding the rare near-tie roundings
 __constant__ float c_dct[64];
+__constant__ double c_dct64[64];
 
 static void ensure_dct_table() {
     static std::mutex mu;
@@ -240,11 +242,15 @@ static void ensure_dct_table() {
     if ((int)done.size() <= dev) done.resize(dev + 1, 0);
     if (done[dev]) return;
     float h[64];
+    double h64[64];
     for (int p = 0; p < 8; ++p)
-        for (int x = 0; x < 8; ++x)
-            h[p * 8 + x] = (float)((p == 0 ? 1.0 / std::sqrt(2.0) : 1.0) * 0.5 *
-                                   std::cos((2 * x + 1) * p * 3.14159265358979323846 / 16.0));
+        for (int x = 0; x < 8; ++x) {
+            h64[p * 8 + x] = (p == 0 ? 1.0 / std::sqrt(2.0) : 1.0) * 0.5 *
+                             std::cos((2 * x + 1) * p * 3.14159265358979323846 / 16.0);
+            h[p * 8 + x] = (float)h64[p * 8 + x];
+        }
     TOMO_CUDA(cudaMemcpyToSymbol(c_dct, h, sizeof(h)));
+    TOMO_CUDA(cudaMemcpyToSymbol(c_dct64, h64, sizeof(h64)));
     done[dev] = 1;
 }
 
@@ -252,15 +258,34 @@ struct QTable {
     int q[64];
 };
 
-// one 8x8 block: src/dst point at its top-left value, `stride` floats per row.
+constexpr int kJpegThreads = 64;
+
+// Bound of the FP32 error of one output of the separable 8x8 transform of
+// inputs x (|basis| <= 1/2, 8 + 8 accumulated FMAs with rounded basis values):
+// 2 gamma_9 (1/2)^2 sum|x| ~ 2.7e-7 sum|x|; taken 4x larger. A rounding
+// decision whose FP32 value lies closer than that to the tie is re-decided
+// in FP64.
+__device__ __forceinline__ float fp32_transform_bound(float sum_abs) { return 1.1e-6f * sum_abs + 1e-6f; }
+
+// distance of x to the nearest half-integer multiple of q: |x| - (k + 1/2) q
+__device__ __forceinline__ float tie_distance(float x, float q) {
+    const float ax = fabsf(x);
+    const float k = floorf(ax / q);
+    return fabsf(ax - (k + 0.5f) * q);
+}
+
+// one 8x8 block: src/dst point at its top-left value, `stride` floats per row;
+// s_smp / s_q: this thread's 64-entry scratch in shared memory, element e at
+// [e * kJpegThreads] (transposed: conflict-free across the warp).
 // Returns the number of non-zero quantized coefficients.
 __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* __restrict__ dst, int stride,
-                                          float lo, float hi, const QTable& qt, int16_t* coefs) {
+                                          float lo, float hi, const QTable& qt, int16_t* coefs,
+                                          int8_t* s_smp, int16_t* s_q) {
     const float rng = __fsub_rn(hi, lo);
     const float inv = __fdiv_rn(255.0f, rng);
     const float step = __fdiv_rn(rng, 255.0f);
     float b[64];
-    float dcs = 0.f;  // sum of the integer samples: exact in FP32
+    float dcs = 0.f, sabs = 0.f;  // sums of the integer samples: exact in FP32
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const float4 v0 = *reinterpret_cast<const float4*>(src + (size_t)i * stride);
@@ -271,7 +296,9 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
             const float t = __fmul_rn(__fsub_rn(v[j], lo), inv);
             const float r = fminf(fmaxf(roundf(t), 0.0f), 255.0f);  // round half away from zero
             b[i * 8 + j] = r - 128.0f;
+            s_smp[(i * 8 + j) * kJpegThreads] = (int8_t)(int)(r - 128.0f);
             dcs += b[i * 8 + j];
+            sabs += fabsf(b[i * 8 + j]);
         }
     }
     // forward DCT: rows, then columns
@@ -302,17 +329,40 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
         }
     }
     b[0] = dcs * 0.125f;  // exact DC term: ties of F00 / Qt are decided exactly
-    int nnz = 0;
+    const float dF = fp32_transform_bound(sabs);
+    unsigned long long near = 0ull;
 #pragma unroll
     for (int e = 0; e < 64; ++e) {
-        float qv = roundf(__fdiv_rn(b[e], (float)qt.q[e]));
-        qv = fminf(fmaxf(qv, -32768.0f), 32767.0f);
+        const float Q = (float)qt.q[e];
+        const float qv = roundf(__fdiv_rn(b[e], Q));
+        if (e != 0 && tie_distance(b[e], Q) < dF) near |= 1ull << e;
+        s_q[e * kJpegThreads] = (int16_t)fminf(fmaxf(qv, -32768.0f), 32767.0f);
+    }
+    while (near) {  // re-decide near-tie coefficients from the samples in FP64
+        const int e = __ffsll((long long)near) - 1;
+        near &= near - 1;
+        const int p = e >> 3, q = e & 7;
+        double F = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < 8; ++j) r = fma((double)s_smp[(i * 8 + j) * kJpegThreads], c_dct64[q * 8 + j], r);
+            F = fma(c_dct64[p * 8 + i], r, F);
+        }
+        s_q[e * kJpegThreads] = (int16_t)fmin(fmax(round(F / (double)qt.q[e]), -32768.0), 32767.0);
+    }
+    int nnz = 0;
+    float gabs = 0.f;
+#pragma unroll
+    for (int e = 0; e < 64; ++e) {
+        const int qv = s_q[e * kJpegThreads];
         if (coefs) coefs[e] = (int16_t)qv;
-        nnz += (qv != 0.0f);
-        b[e] = qv * (float)qt.q[e];  // integer product: exact
+        nnz += (qv != 0);
+        b[e] = (float)(qv * qt.q[e]);  // integer product: exact
+        if (e) gabs += fabsf(b[e]);
     }
     const float dcv = b[0] * 0.125f + 128.0f;  // exact DC contribution + level shift
     b[0] = 0.f;
+    const float dS = fp32_transform_bound(gabs);
     // inverse DCT of the AC part: columns, then rows
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -327,6 +377,7 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
             b[i * 8 + q] = a;
         }
     }
+    near = 0ull;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         float t[8];
@@ -338,11 +389,28 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
             float a = 0.f;
 #pragma unroll
             for (int q = 0; q < 8; ++q) a = fmaf(t[q], c_dct[q * 8 + j], a);
-            const float r = fminf(fmaxf(roundf(a + dcv), 0.0f), 255.0f);
+            const float v = a + dcv;
+            if (fabsf(v - floorf(v) - 0.5f) < dS) near |= 1ull << (i * 8 + j);
+            const float r = fminf(fmaxf(roundf(v), 0.0f), 255.0f);
             o[j] = (r == 255.0f) ? hi : __fadd_rn(lo, __fmul_rn(r, step));
         }
         *reinterpret_cast<float4*>(dst + (size_t)i * stride) = make_float4(o[0], o[1], o[2], o[3]);
         *reinterpret_cast<float4*>(dst + (size_t)i * stride + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    while (near) {  // re-decide near-tie samples from the quantized coefficients in FP64
+        const int e = __ffsll((long long)near) - 1;
+        near &= near - 1;
+        const int i = e >> 3, j = e & 7;
+        double v = 0.0;
+        for (int p = 0; p < 8; ++p) {
+            double r = 0.0;
+            for (int q = 0; q < 8; ++q)
+                if (p | q) r = fma((double)(s_q[(p * 8 + q) * kJpegThreads] * qt.q[p * 8 + q]), c_dct64[q * 8 + j], r);
+            v = fma(c_dct64[p * 8 + i], r, v);
+        }
+        v += (double)(s_q[0] * qt.q[0]) * 0.125 + 128.0;
+        const float r = (float)fmin(fmax(round(v), 0.0), 255.0);
+        dst[(size_t)i * stride + j] = (r == 255.0f) ? hi : __fadd_rn(lo, __fmul_rn(r, step));
     }
     return nnz;
 }
@@ -382,12 +450,12 @@ __global__ void minmax_kernel(const float* in, long long n, float* lohi) {
     }
 }
 
-constexpr int kJpegThreads = 64;
-
 __global__ void __launch_bounds__(kJpegThreads) jpeg_single_kernel(const float* in, int rows, int cols,
                                                                    const QTable qt, int16_t* coefs,
                                                                    const float* lohi, float* deq,
                                                                    long long* nnz) {
+    __shared__ int8_t s_smp[64][kJpegThreads];
+    __shared__ int16_t s_q[64][kJpegThreads];
     const int bpr = cols / 8;
     const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
     int c = 0;
@@ -397,7 +465,7 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_single_kernel(const float* 
         const float lo = lohi[0], hi = lohi[1];
         int16_t* cf = coefs ? coefs + (size_t)blk * 64 : nullptr;
         if (hi > lo) {
-            c = jpeg_block(in + o, deq + o, cols, lo, hi, qt, cf);
+            c = jpeg_block(in + o, deq + o, cols, lo, hi, qt, cf, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
         } else {
             jpeg_const_block(deq + o, cols, lo);
             if (cf)
@@ -412,6 +480,8 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_single_kernel(const float* 
 
 __global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCodec p, const QTable qt,
                                                                   int task_begin) {
+    __shared__ int8_t s_smp[64][kJpegThreads];
+    __shared__ int16_t s_q[64][kJpegThreads];
     const SegTask T = p.tasks[task_begin + blockIdx.y];
     const int N = p.N, bpr = N / 8;
     const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
@@ -426,7 +496,7 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCod
         const float lo = key_float(p.lo_key[T.slice * p.M + T.owner]);
         const float hi = key_float(p.hi_key[T.slice * p.M + T.owner]);
         if (hi > lo)
-            c = jpeg_block(p.xseg + o, dst, N, lo, hi, qt, nullptr);
+            c = jpeg_block(p.xseg + o, dst, N, lo, hi, qt, nullptr, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
         else
             jpeg_const_block(dst, N, lo);
     }

@@ -542,7 +542,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
     int i = ang_begin;
     while (i < end) {
         int na = kProjMaxNa;
-        for (; na > 1; na /= 2) {
+        for (; na >= 1; na /= 2) {
             if (i + na > end) continue;
             const bool cm = rows_major(g.c[angs[i].angle], g.s[angs[i].angle]);
             bool same = true;
@@ -570,6 +570,9 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
             }
             if (ok) break;
         }
+        if (na < 1)  // cannot happen for the limits checked at geometry creation
+            fail(TOMO_ERR_INVALID_ARG, "projector item exceeds the staged extent (angle " +
+                                           std::to_string(angs[i].angle) + ")");
         std::vector<HostProj> As;
         for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
         const int wb = kProjThreads / na;

@@ -97,7 +97,7 @@ struct BpItem {
 
 constexpr int kProjThreads = 256;
 constexpr int kProjRows = 32;   // rows per staged chunk
-constexpr int kProjWMax = 320;  // max staged minor extent
+constexpr int kProjWMax = 400;  // max staged minor extent (256 bins at 45 degrees need 399)
 constexpr int kProjPitch = kProjWMax + 1;
 constexpr int kProjMaxNa = 4;
 

@@ -26,14 +26,19 @@ def gpu_state(s):
 
 
 def compare_states(g_next, o, prob, tol=1e-5, msg_frac=1e-4):
+    """u and x segments at tol; the new messages: identity plane at tol,
+    quantized planes identical except at rounding ties (<= msg_frac of the
+    entries); lambda at tol on every pixel whose new messages agree (a
+    message that differs by one quantization level moves lambda there by
+    rho times that level)"""
     u, lam, xseg, hist, k = g_next
     assert k == o.k
     assert rel_l2(u, o.u) <= tol
-    assert rel_l2(lam, o.lam) <= tol * 10 + 1e-7 * 0  # lambda accumulates rho (u - x)
     assert rel_l2(xseg, o.xseg) <= tol
     slot = o.k % o.D
     kinds = set(np.asarray(prob["home_q"]).tolist()) | set(
         np.asarray(prob["edge_q"])[np.asarray(prob["adj"]) > 0].tolist())
+    agree = np.ones(hist.shape[2:], bool)
     for q in kinds:
         a, b = hist[slot, q], o.hist[slot, q]
         if q == 0:
@@ -41,6 +46,9 @@ def compare_states(g_next, o, prob, tol=1e-5, msg_frac=1e-4):
         else:  # quantized planes: identical levels except at rounding ties
             bad = np.abs(a - b) > 1e-4 * (np.abs(b).max() + 1e-30)
             assert bad.mean() <= msg_frac, (q, bad.mean())
+            agree &= ~bad
+    m = np.broadcast_to(agree[:, None], lam.shape)
+    assert rel_l2(lam[m], o.lam[m]) <= 10 * tol
 
 
 @pytest.mark.parametrize("quant,graph,M", [("none", "ring", 4), ("kmeans", "ring", 4),

@@ -31,6 +31,7 @@ def test_project_and_backproject_match_oracle(N, B, A, off):
     assert rel_l2(d_gpu, og.project(img)) <= TOL
     b_gpu = g.backproject(cuda(sino)).cpu().numpy()
     assert rel_l2(b_gpu, og.backproject(sino)) <= TOL
+    g.close()
 
 
 def test_axis_aligned_single_pixels_are_exact():
@@ -111,3 +112,4 @@ def test_full_size_sampled_rays_and_pixels(name):
     pix = rng.integers(0, N * N, 96)
     ref = og.backproject_pixels(sino, pix)
     assert rel_l2(bp[pix], ref) <= TOL
+    g.close()
