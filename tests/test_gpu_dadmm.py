@@ -143,8 +143,10 @@ def test_stress_config_runs_and_reports():
     the byte count of the wire model"""
     need_gpu()
     p = synth.make_problem("c5_stress")
-    eta = np.full(p["M"], 1.0 / (0.9 * 28 * 2048 + 1.0))
-    s = api.DADMM(p, eta)
+    g = api.Geometry(p["geometry"]["N"], p["geometry"]["B"], p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    L = np.array([g.opnorm_sq(idx[ptr[m]:ptr[m + 1]], iters=10) for m in range(p["M"])])
+    s = api.DADMM(p, 1.0 / (L + p["rho"]), geometry=g)
     st = s.step(torch.as_tensor(p["sino"]).cuda(), 2)
     assert np.all(np.isfinite(st))
     assert np.all(st[:, :, 4] > 0)
