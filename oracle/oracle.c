@@ -321,38 +321,45 @@ void orc_jpeg_qtable(int quality, int32_t* qt) {
     }
 }
 
-/* C(p) C(q) with C(0) = 1/sqrt(2), C(p>0) = 1; the product C(0)^2 is taken as
- * exactly 1/2 so that a block's DC term is an exact multiple of 1/8 */
-static double dct_cc(int p, int q) {
-    if (p == 0 && q == 0) return 0.5;
-    if (p == 0 || q == 0) return 1.0 / sqrt(2.0);
-    return 1.0;
+/* Weight of sample (i, j) in coefficient (p, q) of the orthonormal 2-D
+ * DCT-II: 1/4 C(p) C(q) cos((2i+1) p pi/16) cos((2j+1) q pi/16), C(0) =
+ * 1/sqrt(2). When p and q are both 0 or 4 the weight is exactly +-1/8
+ * (cos((2i+1) pi/4) = +-1/sqrt(2)); it is used exactly, so that these four
+ * coefficients (and image values built from them alone) are exact multiples
+ * of 1/8 and their rounding ties are decided by the rounding rule. */
+static int rational_freq(int p) { return p == 0 || p == 4; }
+
+static double half_sign(int i, int p) { /* sign of cos((2i+1) p pi/16), p in {0, 4} */
+    if (p == 0) return 1.0;
+    const int m = (2 * i + 1) % 8; /* (2i+1) pi/4 modulo 2 pi */
+    return (m == 1 || m == 7) ? 1.0 : -1.0;
 }
 
-/* F[p][q] = 1/4 C(p) C(q) sum_i sum_j f[i][j] cos((2i+1)p pi/16) cos((2j+1)q pi/16) */
+static double dct_weight(int p, int q, int i, int j) {
+    if (rational_freq(p) && rational_freq(q)) return 0.125 * half_sign(i, p) * half_sign(j, q);
+    const double cp = p == 0 ? 1.0 / sqrt(2.0) : 1.0, cq = q == 0 ? 1.0 / sqrt(2.0) : 1.0;
+    return 0.25 * cp * cq * cos((2 * i + 1) * p * ORC_PI / 16.0) * cos((2 * j + 1) * q * ORC_PI / 16.0);
+}
+
+/* F[p][q] = sum_i sum_j f[i][j] w(p, q, i, j) */
 void orc_dct8x8(const double* in, double* out) {
     for (int p = 0; p < 8; ++p)
         for (int q = 0; q < 8; ++q) {
             double acc = 0.0;
             for (int i = 0; i < 8; ++i)
-                for (int j = 0; j < 8; ++j)
-                    acc += in[i * 8 + j] * cos((2 * i + 1) * p * ORC_PI / 16.0) *
-                           cos((2 * j + 1) * q * ORC_PI / 16.0);
-            out[p * 8 + q] = 0.25 * dct_cc(p, q) * acc;
+                for (int j = 0; j < 8; ++j) acc += in[i * 8 + j] * dct_weight(p, q, i, j);
+            out[p * 8 + q] = acc;
         }
 }
 
-/* f[i][j] = 1/4 sum_p sum_q C(p) C(q) F[p][q] cos((2i+1)p pi/16) cos((2j+1)q pi/16) */
+/* f[i][j] = sum_p sum_q F[p][q] w(p, q, i, j) (the transform is orthonormal) */
 void orc_idct8x8(const double* in, double* out) {
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 8; ++j) {
             double acc = 0.0;
             for (int p = 0; p < 8; ++p)
-                for (int q = 0; q < 8; ++q)
-                    acc += dct_cc(p, q) * in[p * 8 + q] *
-                           cos((2 * i + 1) * p * ORC_PI / 16.0) *
-                           cos((2 * j + 1) * q * ORC_PI / 16.0);
-            out[i * 8 + j] = 0.25 * acc;
+                for (int q = 0; q < 8; ++q) acc += in[p * 8 + q] * dct_weight(p, q, i, j);
+            out[i * 8 + j] = acc;
         }
 }
 

@@ -161,3 +161,20 @@ def test_jpeg_error_bounded_by_dequantization_step():
     step = (lohi[1] - lohi[0]) / 255.0
     assert np.max(np.abs(deq - seg)) <= 2.0 * step
     assert nnz == int(np.count_nonzero(coefs))
+
+
+def test_rational_coefficient_ties_round_half_away():
+    """rows alternating +3/-3 in the pattern of cos((2i+1) pi/4): the only
+    non-zero coefficient is F[4][0] = (1/8) * 64 * 3 = 24 exactly; at quality
+    55 its table entry is 16, so F / Q = 1.5 is an exact tie and must round
+    away from zero to 2; the decoded rows are 128 +- 32/8"""
+    sig = np.array([1, -1, -1, 1, 1, -1, -1, 1])
+    seg = np.zeros((8, 16), np.float32)
+    seg[:, :8] = (128 + 3 * sig)[:, None]
+    seg[0, 8], seg[1, 8] = 0.0, 255.0  # lo = 0, hi = 255: samples equal the values
+    assert O.jpeg_qtable(55)[4, 0] == 16
+    F = O.dct8x8(seg[:, :8].astype(np.float64) - 128.0)
+    assert F[4, 0] == 24.0 and np.all(np.abs(np.delete(F.ravel(), 32)) < 1e-12)
+    coefs, _, deq, _ = O.jpeg(seg, 55)
+    assert coefs[0, 32] == 2 and np.count_nonzero(coefs[0]) == 1
+    assert np.array_equal(deq[:, :8], np.broadcast_to((128 + 4 * sig)[:, None], (8, 8)).astype(np.float32))
