@@ -267,6 +267,12 @@ constexpr int kJpegThreads = 64;
 // in FP64.
 __device__ __forceinline__ float fp32_transform_bound(float sum_abs) { return 1.1e-6f * sum_abs + 1e-6f; }
 
+// sign of cos((2i+1) pi / 4): the basis of frequency 4 up to 1/(2 sqrt 2)
+__device__ constexpr float kSigma4[8] = {1.f, -1.f, -1.f, 1.f, 1.f, -1.f, -1.f, 1.f};
+
+// coefficients (p, q) with p, q in {0, 4}: weights +-1/8, rational values
+__device__ __forceinline__ bool is_rational(int e) { return e == 0 || e == 4 || e == 32 || e == 36; }
+
 // distance of x to the nearest half-integer multiple of q: |x| - (k + 1/2) q
 __device__ __forceinline__ float tie_distance(float x, float q) {
     const float ax = fabsf(x);
@@ -285,21 +291,29 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
     const float inv = __fdiv_rn(255.0f, rng);
     const float step = __fdiv_rn(rng, 255.0f);
     float b[64];
-    float dcs = 0.f, sabs = 0.f;  // sums of the integer samples: exact in FP32
+    // integer sums of the samples (exact in FP32): the coefficients (0,0),
+    // (0,4), (4,0), (4,4) have weights +-1/8 and are formed exactly from them
+    float f00 = 0.f, f04 = 0.f, f40 = 0.f, f44 = 0.f, sabs = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const float4 v0 = *reinterpret_cast<const float4*>(src + (size_t)i * stride);
         const float4 v1 = *reinterpret_cast<const float4*>(src + (size_t)i * stride + 4);
         const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        float rs = 0.f, r4 = 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const float t = __fmul_rn(__fsub_rn(v[j], lo), inv);
             const float r = fminf(fmaxf(roundf(t), 0.0f), 255.0f);  // round half away from zero
             b[i * 8 + j] = r - 128.0f;
             s_smp[(i * 8 + j) * kJpegThreads] = (int8_t)(int)(r - 128.0f);
-            dcs += b[i * 8 + j];
+            rs += b[i * 8 + j];
+            r4 += kSigma4[j] * b[i * 8 + j];
             sabs += fabsf(b[i * 8 + j]);
         }
+        f00 += rs;
+        f40 += kSigma4[i] * rs;
+        f04 += r4;
+        f44 += kSigma4[i] * r4;
     }
     // forward DCT: rows, then columns
 #pragma unroll
@@ -328,14 +342,17 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
             b[p * 8 + q] = a;
         }
     }
-    b[0] = dcs * 0.125f;  // exact DC term: ties of F00 / Qt are decided exactly
+    b[0] = f00 * 0.125f;  // exact: ties of F / Qt are decided by the rounding rule
+    b[4] = f04 * 0.125f;
+    b[32] = f40 * 0.125f;
+    b[36] = f44 * 0.125f;
     const float dF = fp32_transform_bound(sabs);
     unsigned long long near = 0ull;
 #pragma unroll
     for (int e = 0; e < 64; ++e) {
         const float Q = (float)qt.q[e];
         const float qv = roundf(__fdiv_rn(b[e], Q));
-        if (e != 0 && tie_distance(b[e], Q) < dF) near |= 1ull << e;
+        if (!is_rational(e) && tie_distance(b[e], Q) < dF) near |= 1ull << e;
         s_q[e * kJpegThreads] = (int16_t)fminf(fmaxf(qv, -32768.0f), 32767.0f);
     }
     while (near) {  // re-decide near-tie coefficients from the samples in FP64
@@ -358,10 +375,11 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
         if (coefs) coefs[e] = (int16_t)qv;
         nnz += (qv != 0);
         b[e] = (float)(qv * qt.q[e]);  // integer product: exact
-        if (e) gabs += fabsf(b[e]);
+        if (!is_rational(e)) gabs += fabsf(b[e]);
     }
-    const float dcv = b[0] * 0.125f + 128.0f;  // exact DC contribution + level shift
-    b[0] = 0.f;
+    // the rational part of every output value, exact: (G00 + s4(j) G04 + s4(i) G40 + s4(i) s4(j) G44) / 8
+    const float g00 = b[0], g04 = b[4], g40 = b[32], g44 = b[36];
+    b[0] = b[4] = b[32] = b[36] = 0.f;
     const float dS = fp32_transform_bound(gabs);
     // inverse DCT of the AC part: columns, then rows
 #pragma unroll
@@ -384,12 +402,14 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
 #pragma unroll
         for (int q = 0; q < 8; ++q) t[q] = b[i * 8 + q];
         float o[8];
+        const float ra = g00 + kSigma4[i] * g40, rb = g04 + kSigma4[i] * g44;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             float a = 0.f;
 #pragma unroll
             for (int q = 0; q < 8; ++q) a = fmaf(t[q], c_dct[q * 8 + j], a);
-            const float v = a + dcv;
+            const float rat = (ra + kSigma4[j] * rb) * 0.125f + 128.0f;  // exact
+            const float v = a + rat;
             if (fabsf(v - floorf(v) - 0.5f) < dS) near |= 1ull << (i * 8 + j);
             const float r = fminf(fmaxf(roundf(v), 0.0f), 255.0f);
             o[j] = (r == 255.0f) ? hi : __fadd_rn(lo, __fmul_rn(r, step));
@@ -405,10 +425,12 @@ __device__ __forceinline__ int jpeg_block(const float* __restrict__ src, float* 
         for (int p = 0; p < 8; ++p) {
             double r = 0.0;
             for (int q = 0; q < 8; ++q)
-                if (p | q) r = fma((double)(s_q[(p * 8 + q) * kJpegThreads] * qt.q[p * 8 + q]), c_dct64[q * 8 + j], r);
+                if (!is_rational(p * 8 + q))
+                    r = fma((double)(s_q[(p * 8 + q) * kJpegThreads] * qt.q[p * 8 + q]), c_dct64[q * 8 + j], r);
             v = fma(c_dct64[p * 8 + i], r, v);
         }
-        v += (double)(s_q[0] * qt.q[0]) * 0.125 + 128.0;
+        v += ((double)g00 + kSigma4[i] * (double)g40 + kSigma4[j] * ((double)g04 + kSigma4[i] * (double)g44)) * 0.125 +
+             128.0;
         const float r = (float)fmin(fmax(round(v), 0.0), 255.0);
         dst[(size_t)i * stride + j] = (r == 255.0f) ? hi : __fadd_rn(lo, __fmul_rn(r, step));
     }

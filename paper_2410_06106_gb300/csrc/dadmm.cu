@@ -443,8 +443,12 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
                               cudaStream_t s) {
     const bool batched = h.mode == DADMM_MODE_BATCHED;
     int phase = 0;
-    auto mark = [&]() {  // boundary before phase `phase`
-        if (h.profiling) TOMO_CUDA(cudaEventRecord(h.pev[phase], s));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TOMO_CUDA(cudaStreamIsCapturing(s, &cap));
+    auto mark = [&]() {  // boundary before phase `phase`; a graph node when capturing
+        if (h.profiling)
+            TOMO_CUDA(cudaEventRecordWithFlags(h.pev[phase], s,
+                                               cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0));
         ++phase;
     };
     const size_t SM = (size_t)h.S * h.M;
