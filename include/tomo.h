@@ -94,6 +94,26 @@ TOMO_API tomo_status tomo_project(tomo_geometry_t g, const float* img, float* si
                          const int32_t* angle_idx, int n_sel, int batch,
                          const float* subtract, tomo_stream_t stream);
 
+/* Forward projection that allocates no device memory. The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc
+ * (code running while a CUDA graph is being captured elsewhere in the
+ * process, code bound to a fixed memory budget or pool, real-time loops that
+ * forbid allocation after start-up). Same arguments, layouts and result as
+ * tomo_project; the work list lives in a fixed array inside the library's
+ * device image instead of memory the library allocates, so the call performs
+ * no cudaMalloc/cudaFree and no allocating library routine.
+ * Limits: n_sel <= 8192 angles and at most 16384 work items (about
+ * batch * ceil(n_sel / 4) * ceil(B / 64)); larger requests return
+ * TOMO_ERR_WORKSPACE with a message and launch nothing. The array (576 KiB)
+ * is held on every GPU that loads the library until the process exits.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture. Every call reuses the same
+ * array and leaves its work list there: calls that overlap on the GPU (other
+ * streams, or other host threads) race and must be serialized by the caller. */
+TOMO_API tomo_status tomo_project_noalloc(tomo_geometry_t g, const float* img, float* sino,
+                                          const int32_t* angle_idx, int n_sel, int batch,
+                                          const float* subtract, tomo_stream_t stream);
+
 /* Matched backprojection (the exact transpose of tomo_project's matrix):
  *   img[k][i][j] = beta * img[k][i][j] + sum_{q,b} P[(angle_idx[q], b),(i,j)] sino[k][q][b]
  * beta must be 0 or 1 (0: img is not read). Same layouts and ownership as

@@ -54,6 +54,8 @@ SIGNATURES = {
     "tomo_geometry_destroy": (C.c_int, [C.c_void_p]),
     "tomo_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                C.c_void_p, C.c_void_p]),
+    "tomo_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                       C.c_void_p, C.c_void_p]),
     "tomo_backproject": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                    C.c_float, C.c_void_p]),
     "tomo_opnorm_workspace_size": (C.c_size_t, [C.c_void_p, C.c_int]),
