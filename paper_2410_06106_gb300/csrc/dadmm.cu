@@ -730,12 +730,10 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                         h->b_range[2 * sn + 1] = (int)bplain.size();
                     }
                 }
+            // batched order: node-major, as the plain lists, so that the blocks in flight
+            // work on few nodes at a time and each node's image stays in L2
             std::vector<ProjItem> pb = pplain;
             std::vector<BpItem> bb = bplain;
-            std::stable_sort(pb.begin(), pb.end(), [](const ProjItem& x, const ProjItem& y) {
-                return x.nchunks * x.na > y.nchunks * y.na;
-            });
-            std::stable_sort(bb.begin(), bb.end(), [](const BpItem& x, const BpItem& y) { return x.na > y.na; });
             h->d_angs = device_upload(angs);
             h->d_pitems = device_upload(pb);
             h->d_bitems = device_upload(bb);

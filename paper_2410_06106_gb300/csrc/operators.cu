@@ -96,14 +96,28 @@ void check_device(const Geometry& g) {
 // ------------------------------------------------------------------
 // per-angle parameters, derived in FP64 from the constant table
 // ------------------------------------------------------------------
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic rounds x to an integer
-constexpr int kMagicI = 0x4B400000;    // bit pattern of kMagic
 constexpr float kGammaCap = 1048576.0f;  // 2^20
+constexpr double kFix25 = 33554432.0;    // 2^25: fixed point of positions inside a block
+constexpr int kFracBits = 25;
+
+// 1 + (fraction of a 2^-25 fixed-point position) as a float in [1, 2): the
+// top 23 of the 25 fraction bits become the mantissa (exact for the
+// half-integer positions of axis-aligned rays)
+__device__ __forceinline__ float one_plus_frac25(int p) {
+    return __int_as_float(((p >> 2) & 0x7FFFFF) | 0x3F800000);
+}
+
+// Weights of the two candidate pixels/bins around a position with fraction
+// f = F - 1 (distance to the lower candidate, in minor units): the trapezoid
+// h sat(0.5 + g (w_mid - dist)) with g the slope in those units gives
+//   w_lower = sat(wf0 - g F), w_upper = sat(wf1 + g F),
+//   wf0 = 0.5 + g (w_mid + 1), wf1 = 0.5 + g (w_mid - 2).
 
 struct ProjAngle {
     long long Db, Dm, K0;  // minor coordinate of ray b at major index m: b Db + m Dm + K0 (2^-40)
-    float dm;              // Dm in FP32, for stepping inside a chunk
-    float kappa;           // |major| / |minor|: slope of the weight in minor-index units
+    int dm25;              // Dm in 2^-25, for stepping inside a chunk
+    float kappa;           // |major| / |minor|: the weight slope in minor-index units
+    float wf0, wf1;        // weight constants (w_mid = 1/2 in minor units)
     float h;               // 1 / |major|
     int colmaj;            // 0: image rows are the major axis; 1: columns
 };
@@ -131,46 +145,88 @@ __device__ __forceinline__ ProjAngle proj_angle(int N, int B, double2 cs) {
     r.Db = __double2ll_rn(db * kFix);
     r.Dm = __double2ll_rn(dm * kFix);
     r.K0 = __double2ll_rn(k0 * kFix);
-    r.dm = (float)dm;
-    r.kappa = mnr > 0.0 ? (float)(maj / mnr) : kGammaCap;
+    r.dm25 = (int)__double2ll_rn(dm * kFix25);
+    const double kap = mnr > 0.0 ? maj / mnr : (double)kGammaCap;
+    r.kappa = (float)kap;
+    r.wf0 = (float)(0.5 + kap * 1.5);
+    r.wf1 = (float)(0.5 - kap * 1.5);
     r.h = (float)(1.0 / maj);
     return r;
 }
 
 struct BpAngle {
-    long long C, S, K;  // bin coordinate of pixel (i, j): j C - i S + K (2^-40)
-    float c, s;         // FP32 steps for the pixels of one thread
-    float gam, alpha;   // weight = sat(alpha -+ gam e) in bin units
-    float h;            // folded into the staged sinogram values
-    int w0;             // first staged bin of this tile
-    const float* row;   // sinogram line
+    unsigned P0;       // bin coordinate of the tile's first pixel minus w0 (2^-25)
+    int C25, S25;      // cos, sin (2^-25): the steps of one pixel in x and y
+    int w0;            // first staged bin of this tile
+    float gam;         // weight slope in bin units, 1/min(|c|,|s|) (capped)
+    float wf0, wf1;    // weight constants (w_mid = max(|c|,|s|)/2)
+    float h;           // 1/max(|c|,|s|), folded into the staged sinogram values
+    const float* row;  // sinogram line
 };
 
-__device__ __forceinline__ void bp_angle(BpAngle& r, int N, int B, double2 cs) {
+// tile origin (x0, y0), tile extent kBpTileX x kBpTileY
+__device__ __forceinline__ void bp_angle(BpAngle& r, int N, int B, double2 cs, int x0, int y0) {
     const double c = cs.x, s = cs.y, hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
     const double ac = fabs(c), as = fabs(s);
     const double mx = fmax(ac, as), mn = fmin(ac, as);
-    r.C = __double2ll_rn(c * kFix);
-    r.S = __double2ll_rn(s * kFix);
-    r.K = __double2ll_rn((hB - hN * c + hN * s) * kFix);
-    r.c = (float)c;
-    r.s = (float)s;
+    // bin coordinate of pixel (i, j): j c - i s + (hB - hN c + hN s), in 2^-40
+    const long long C = __double2ll_rn(c * kFix), S = __double2ll_rn(s * kFix);
+    const long long K = __double2ll_rn((hB - hN * c + hN * s) * kFix);
+    long long lo = LLONG_MAX;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long j = x0 + ((k & 1) ? kBpTileX - 1 : 0);
+        const long long i = y0 + ((k & 2) ? kBpTileY - 1 : 0);
+        lo = min(lo, j * C - i * S + K);
+    }
+    r.w0 = (int)(lo >> 40) - 2;
+    const long long org = (long long)x0 * C - (long long)y0 * S + K;
+    r.P0 = (unsigned)((org - ((long long)r.w0 << 40)) >> 15);
+    r.C25 = (int)__double2ll_rn(c * kFix25);
+    r.S25 = (int)__double2ll_rn(s * kFix25);
     const double gam = mn > 0.0 ? 1.0 / mn : (double)kGammaCap;
     r.gam = (float)gam;
-    r.alpha = (float)(0.5 + gam * (0.5 * mx - 0.5));
+    r.wf0 = (float)(0.5 + gam * (0.5 * mx + 1.0));
+    r.wf1 = (float)(0.5 + gam * (0.5 * mx - 2.0));
     r.h = (float)(1.0 / mx);
 }
 
-__device__ __forceinline__ float frac40_to_float(long long p) {
-    // top 23 bits of the 40-bit fraction as a float in [0, 1)
-    return __int_as_float(0x3F800000 | (int)((p >> 17) & 0x7FFFFF)) - 1.0f;
+// asynchronous 4-byte global -> shared copy; zero-fill when !valid
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ------------------------------------------------------------------
 // projector
 // ------------------------------------------------------------------
+
+// thread -> (angle slot, bin offset) of an item of na angles x 256/na bins.
+// na = 4: warp w takes bins 16 (w & 3) .. + 16 of angles 2 (w >> 2) and +1;
+// na = 2: warp w takes bins 16 w .. + 16 of both angles; na = 1: 32 bins.
+// Half-warps of adjacent angles read nearly the same shared words, so a
+// warp touches few banks twice.
+__device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& boff) {
+    const int lane = tid & 31, warp = tid >> 5;
+    if (na == 1) {
+        slot = 0;
+        boff = tid;
+    } else if (na == 2) {
+        slot = lane >> 4;
+        boff = 16 * warp + (lane & 15);
+    } else {
+        slot = 2 * (warp >> 2) + (lane >> 4);
+        boff = 16 * (warp & 3) + (lane & 15);
+    }
+}
+
 __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams p) {
-    extern __shared__ float tile[];  // [kProjRows][kProjPitch]
+    extern __shared__ __align__(16) float tile[];  // [kProjRows][kProjPitch]
     __shared__ ProjAngle sa[kProjMaxNa];
     __shared__ int s_item, s_q0, s_w;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -192,16 +248,19 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
         __syncthreads();
 
         const int na = item.na, wb = kProjThreads / na;
-        const int slot = tid / wb;
-        const int b = item.b0 + tid % wb;
+        int slot, boff;
+        proj_lane_map(na, tid, slot, boff);
+        const int b = item.b0 + boff;
         const int blast = min(item.b0 + wb - 1, B - 1);
         const int bc = min(b, blast);  // rays past the last bin shadow it (their output is dropped)
         const ProjAngle A = sa[slot];
         const int colmaj = sa[0].colmaj;
         const float* img = p.img + (size_t)item.img * n;
+        long long pos = (long long)bc * A.Db + (long long)item.m_lo * A.Dm + A.K0;  // at the first chunk
+        const long long dpos = (long long)kProjRows * A.Dm;
         float total = 0.f;
 
-        for (int ch = 0; ch < item.nchunks; ++ch) {
+        for (int ch = 0; ch < item.nchunks; ++ch, pos += dpos) {
             const int m0 = item.m_lo + ch * kProjRows;
             if (warp == 0) {  // staged minor range: extremes over the item's corner rays
                 long long lo = LLONG_MAX, hi = LLONG_MIN;
@@ -229,42 +288,45 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
                 __syncthreads();  // every thread has read s_q0 / s_w
                 continue;
             }
+            // stage the band the item's rays cross (zero outside the image), asynchronously
             if (!colmaj) {
                 for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
                     const int row = m0 + r;
-                    const bool rok = row >= 0 && row < N;
+                    const bool rok = (unsigned)row < (unsigned)N;
                     const float* src = img + (size_t)(rok ? row : 0) * N;
+                    float* dst = tile + r * kProjPitch;
                     for (int q = lane; q < w; q += 32) {
                         const int col = q0 + q;
-                        tile[r * kProjPitch + q] = (rok && col >= 0 && col < N) ? __ldg(src + col) : 0.f;
+                        const bool ok = rok && (unsigned)col < (unsigned)N;
+                        cp_async4(dst + q, ok ? src + col : img, ok);
                     }
                 }
             } else {
                 const int col = m0 + lane;
-                const bool cok = col >= 0 && col < N;
+                const bool cok = (unsigned)col < (unsigned)N;
                 for (int q = warp; q < w; q += kProjThreads / 32) {
                     const int row = q0 + q;
-                    tile[lane * kProjPitch + q] =
-                        (cok && row >= 0 && row < N) ? __ldg(img + (size_t)row * N + col) : 0.f;
+                    const bool ok = cok && (unsigned)row < (unsigned)N;
+                    cp_async4(tile + lane * kProjPitch + q, ok ? img + (size_t)row * N + col : img, ok);
                 }
             }
+            cp_async_wait_all();
             __syncthreads();
 
-            const long long pos = (long long)bc * A.Db + (long long)m0 * A.Dm + A.K0;
-            const int off = ((int)(pos >> 40) - q0) - kMagicI;
-            const float fm = frac40_to_float(pos) - 0.5f;
+            // this ray: integer part J and 2^-25 fraction of its position at row m0
+            const int J = (int)(pos >> 40);
+            const int f0 = (int)((pos >> 15) & 0x1FFFFFF);
+            const float* base = tile + (J - q0);
             float acc = 0.f;
 #pragma unroll
             for (int r = 0; r < kProjRows; ++r) {
-                const float pm = fmaf((float)r, A.dm, fm);  // ray centre - 1/2, minor units
-                const float q = pm + kMagic;                 // rint(pm) + kMagic
-                const float e = pm - (q - kMagic);           // in [-1/2, 1/2]
-                const float* t = tile + r * kProjPitch + (__float_as_int(q) + off);
-                const float u0 = t[0], u1 = t[1];
-                const float w0 = __saturatef(fmaf(-A.kappa, e, 0.5f));
-                const float w1 = __saturatef(fmaf(A.kappa, e, 0.5f));
-                acc = fmaf(w0, u0, acc);
-                acc = fmaf(w1, u1, acc);
+                const int pl = f0 + r * A.dm25;  // position - J at row m0 + r (2^-25), may be negative
+                const float F = one_plus_frac25(pl);
+                const float* t = base + r * kProjPitch + (pl >> kFracBits);  // lower candidate pixel
+                const float w0 = __saturatef(fmaf(-A.kappa, F, A.wf0));
+                const float w1 = __saturatef(fmaf(A.kappa, F, A.wf1));
+                acc = fmaf(w0, t[0], acc);
+                acc = fmaf(w1, t[1], acc);
             }
             total += acc;
         }
@@ -285,15 +347,16 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
 // ------------------------------------------------------------------
 enum { EPI_STORE = 0, EPI_USTEP = 1 };
 
+// 16 x 16 threads; thread (tx, ty) owns the 4 x 4 pixels (x0 + tx + 16 kx,
+// y0 + ty + 16 ky): a half-warp (16 consecutive tx) reads 16 window pairs
+// within 16 consecutive entries, so its 64-bit shared loads never conflict.
 template <int EPI>
 __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams p) {
-    __shared__ float2 win[kBpChunk][kBpWin];  // (v[b], v[b+1]) pairs, h folded in
+    __shared__ __align__(16) float2 win[kBpChunk][kBpWin];  // (h v[b], h v[b+1])
     __shared__ BpAngle sa[kBpChunk];
     __shared__ int s_item;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // 16 x 16 threads, each 4 (x) x 2 (y) pixels; a warp covers 32 x 8 pixels
-    const int tx = (lane & 7) + 8 * (warp & 1);
-    const int ty = (lane >> 3) + 4 * (warp >> 1);
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
     const int N = p.N, B = p.B;
     const size_t n = (size_t)N * N;
 
@@ -309,10 +372,9 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
         if (it >= p.n_items) break;
         const BpItem item = p.items[it];
         const int x0 = item.tx * kBpTileX, y0 = item.ty * kBpTileY;
-        const int px = x0 + 4 * tx, py = y0 + 2 * ty;  // this thread's first pixel (column, row)
-        float acc[2][4];
+        float acc[4][4];
 #pragma unroll
-        for (int ky = 0; ky < 2; ++ky)
+        for (int ky = 0; ky < 4; ++ky)
 #pragma unroll
             for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
 
@@ -321,46 +383,36 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
             if (tid < nac) {
                 BpAngle& A = sa[tid];
                 const AngRow ar = p.angs[item.ang0 + a0 + tid];
-                bp_angle(A, N, B, c_trig[p.const_off + ar.angle]);
+                bp_angle(A, N, B, c_trig[p.const_off + ar.angle], x0, y0);
                 A.row = p.sino + ((size_t)item.sinb + ar.row) * B;
-                // lowest bin coordinate over the tile corners, minus a margin
-                long long lo = LLONG_MAX;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const long long j = x0 + ((k & 1) ? kBpTileX - 1 : 0);
-                    const long long i = y0 + ((k & 2) ? kBpTileY - 1 : 0);
-                    lo = min(lo, j * A.C - i * A.S + A.K);
-                }
-                A.w0 = (int)(lo >> 40) - 2;
             }
             __syncthreads();
             for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
                 const int a = e / kBpWin, k = e - a * kBpWin;
                 const BpAngle& A = sa[a];
                 const int b = A.w0 + k;
-                const float v0 = (b >= 0 && b < B) ? __ldg(A.row + b) : 0.f;
-                const float v1 = (b + 1 >= 0 && b + 1 < B) ? __ldg(A.row + b + 1) : 0.f;
+                const float v0 = ((unsigned)b < (unsigned)B) ? __ldg(A.row + b) : 0.f;
+                const float v1 = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(A.row + b + 1) : 0.f;
                 win[a][k] = make_float2(A.h * v0, A.h * v1);
             }
             __syncthreads();
             for (int a = 0; a < nac; ++a) {
                 const BpAngle& A = sa[a];
-                const long long pfx = (long long)px * A.C - (long long)py * A.S + A.K;
-                const int off = ((int)(pfx >> 40) - A.w0) - kMagicI;
-                const float fm = frac40_to_float(pfx) - 0.5f;
                 const float2* wa = win[a];
-                const float c = A.c, s = A.s, gam = A.gam, alpha = A.alpha;
+                const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
+                // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
+                const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
+                const unsigned cx = (unsigned)A.C25 << 4, sy = (unsigned)A.S25 << 4;
 #pragma unroll
-                for (int ky = 0; ky < 2; ++ky) {
-                    const float rowm = fmaf(-(float)ky, s, fm);
+                for (int ky = 0; ky < 4; ++ky) {
+                    const unsigned prow = pb - (unsigned)ky * sy;
 #pragma unroll
                     for (int kx = 0; kx < 4; ++kx) {
-                        const float pm = fmaf((float)kx, c, rowm);  // bin coordinate - 1/2
-                        const float q = pm + kMagic;
-                        const float e = pm - (q - kMagic);
-                        const float2 r = wa[__float_as_int(q) + off];
-                        const float w0 = __saturatef(fmaf(-gam, e, alpha));
-                        const float w1 = __saturatef(fmaf(gam, e, alpha));
+                        const unsigned pp = prow + (unsigned)kx * cx;
+                        const float F = one_plus_frac25((int)pp);
+                        const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
+                        const float w0 = __saturatef(fmaf(-gam, F, wf0));
+                        const float w1 = __saturatef(fmaf(gam, F, wf1));
                         acc[ky][kx] = fmaf(w0, r.x, acc[ky][kx]);
                         acc[ky][kx] = fmaf(w1, r.y, acc[ky][kx]);
                     }
@@ -372,12 +424,12 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
         if (EPI == EPI_STORE) {
             float* img = p.img + (size_t)item.img * n;
 #pragma unroll
-            for (int ky = 0; ky < 2; ++ky) {
-                const int row = py + ky;
+            for (int ky = 0; ky < 4; ++ky) {
+                const int row = y0 + ty + 16 * ky;
                 if (row >= N) continue;
 #pragma unroll
                 for (int kx = 0; kx < 4; ++kx) {
-                    const int col = px + kx;
+                    const int col = x0 + tx + 16 * kx;
                     if (col >= N) continue;
                     float* o = img + (size_t)row * N + col;
                     *o = (p.beta != 0.f ? *o : 0.f) + acc[ky][kx];
@@ -391,8 +443,8 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
             float* u = V.u + (size_t)item.img * n;
             const float* lam = V.lam + (size_t)item.img * n;
 #pragma unroll
-            for (int ky = 0; ky < 2; ++ky) {
-                const int row = py + ky;
+            for (int ky = 0; ky < 4; ++ky) {
+                const int row = y0 + ty + 16 * ky;
                 if (row >= N) continue;
                 const int seg = V.seg_of_row[row];
                 const int mi = item.node * V.M + seg;
@@ -403,7 +455,7 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
                          (size_t)row * N;
 #pragma unroll
                 for (int kx = 0; kx < 4; ++kx) {
-                    const int col = px + kx;
+                    const int col = x0 + tx + 16 * kx;
                     if (col >= N) continue;
                     const size_t o = (size_t)row * N + col;
                     const float uo = u[o];

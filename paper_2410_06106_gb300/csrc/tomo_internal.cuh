@@ -85,7 +85,7 @@ struct ProjItem {
     int pad;
 };
 
-// backprojector work item: one 64 x 32 pixel tile of one image, all the
+// backprojector work item: one 64 x 64 pixel tile of one image, all the
 // angles of an AngRow run
 struct BpItem {
     int img;   // image index (units of N*N floats); also the u/lambda index in dADMM
@@ -98,13 +98,13 @@ struct BpItem {
 constexpr int kProjThreads = 256;
 constexpr int kProjRows = 32;   // rows per staged chunk
 constexpr int kProjWMax = 400;  // max staged minor extent (256 bins at 45 degrees need 399)
-constexpr int kProjPitch = kProjWMax + 1;
+constexpr int kProjPitch = kProjWMax + 4;  // rows stay 16-byte aligned; 404 = 20 (mod 32) banks apart
 constexpr int kProjMaxNa = 4;
 
 constexpr int kBpThreads = 256;
-constexpr int kBpTileX = 64, kBpTileY = 32;
+constexpr int kBpTileX = 64, kBpTileY = 64;
 constexpr int kBpChunk = 32;  // angles staged per pass
-constexpr int kBpWin = 80;    // window pairs per angle
+constexpr int kBpWin = 96;    // window pairs per angle: 63 (|c| + |s|) + 6 < 96
 
 constexpr double kFix = 1099511627776.0;  // 2^40, fixed-point scale of positions
 
