@@ -198,6 +198,12 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
                  : "memory");
 }
 
+// asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -282,7 +288,8 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
                 }
             }
             __syncthreads();  // previous chunk fully consumed; s_q0/s_w visible
-            const int q0 = s_q0, w = s_w;
+            int q0 = s_q0;
+            const int w = s_w;
             if (w > kProjWMax) {  // unreachable: the host bounds every item's extent
                 if (tid == 0 && p.status) atomicOr(p.status, 1);
                 __syncthreads();  // every thread has read s_q0 / s_w
@@ -290,15 +297,27 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
             }
             // stage the band the item's rays cross (zero outside the image), asynchronously
             if (!colmaj) {
+                // rows: the band starts at a multiple of 4 columns so that whole
+                // 16-byte groups inside the image are copied at once
+                q0 &= ~3;
+                const int ng = (s_q0 + w - q0 + 3) >> 2;  // 16-byte groups per row (<= kProjPitch / 4)
+                const bool vec = (N & 3) == 0;
                 for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
                     const int row = m0 + r;
                     const bool rok = (unsigned)row < (unsigned)N;
                     const float* src = img + (size_t)(rok ? row : 0) * N;
                     float* dst = tile + r * kProjPitch;
-                    for (int q = lane; q < w; q += 32) {
-                        const int col = q0 + q;
-                        const bool ok = rok && (unsigned)col < (unsigned)N;
-                        cp_async4(dst + q, ok ? src + col : img, ok);
+                    for (int g = lane; g < ng; g += 32) {
+                        const int col = q0 + 4 * g;
+                        if (vec && rok && col >= 0 && col + 4 <= N) {
+                            cp_async16(dst + 4 * g, src + col);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const bool ok = rok && (unsigned)(col + e) < (unsigned)N;
+                                cp_async4(dst + 4 * g + e, ok ? src + col + e : img, ok);
+                            }
+                        }
                     }
                 }
             } else {
@@ -351,7 +370,7 @@ enum { EPI_STORE = 0, EPI_USTEP = 1 };
 // y0 + ty + 16 ky): a half-warp (16 consecutive tx) reads 16 window pairs
 // within 16 consecutive entries, so its 64-bit shared loads never conflict.
 template <int EPI>
-__global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams p) {
+__global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
     __shared__ __align__(16) float2 win[kBpChunk][kBpWin];  // (h v[b], h v[b+1])
     __shared__ BpAngle sa[kBpChunk];
     __shared__ int s_item;
@@ -387,13 +406,37 @@ __global__ void __launch_bounds__(kBpThreads) backproject_kernel(const BpParams 
                 A.row = p.sino + ((size_t)item.sinb + ar.row) * B;
             }
             __syncthreads();
-            for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
-                const int a = e / kBpWin, k = e - a * kBpWin;
-                const BpAngle& A = sa[a];
-                const int b = A.w0 + k;
-                const float v0 = ((unsigned)b < (unsigned)B) ? __ldg(A.row + b) : 0.f;
-                const float v1 = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(A.row + b + 1) : 0.f;
-                win[a][k] = make_float2(A.h * v0, A.h * v1);
+            if (nac == kBpChunk) {  // full chunk: fixed trip count, loads in flight together
+                constexpr int kPer = kBpChunk * kBpWin / kBpThreads, kHalf = kPer / 2;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float v0[kHalf], v1[kHalf];
+#pragma unroll
+                    for (int i = 0; i < kHalf; ++i) {
+                        const int e = tid + (half * kHalf + i) * kBpThreads;
+                        const int a = e / kBpWin, k = e - a * kBpWin;
+                        const int b = sa[a].w0 + k;
+                        const float* row = sa[a].row;
+                        v0[i] = ((unsigned)b < (unsigned)B) ? __ldg(row + b) : 0.f;
+                        v1[i] = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(row + b + 1) : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kHalf; ++i) {
+                        const int e = tid + (half * kHalf + i) * kBpThreads;
+                        const int a = e / kBpWin, k = e - a * kBpWin;
+                        const float h = sa[a].h;
+                        win[a][k] = make_float2(h * v0[i], h * v1[i]);
+                    }
+                }
+            } else {
+                for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
+                    const int a = e / kBpWin, k = e - a * kBpWin;
+                    const BpAngle& A = sa[a];
+                    const int b = A.w0 + k;
+                    const float v0 = ((unsigned)b < (unsigned)B) ? __ldg(A.row + b) : 0.f;
+                    const float v1 = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(A.row + b + 1) : 0.f;
+                    win[a][k] = make_float2(A.h * v0, A.h * v1);
+                }
             }
             __syncthreads();
             for (int a = 0; a < nac; ++a) {

@@ -98,7 +98,7 @@ struct BpItem {
 constexpr int kProjThreads = 256;
 constexpr int kProjRows = 32;   // rows per staged chunk
 constexpr int kProjWMax = 400;  // max staged minor extent (256 bins at 45 degrees need 399)
-constexpr int kProjPitch = kProjWMax + 4;  // rows stay 16-byte aligned; 404 = 20 (mod 32) banks apart
+constexpr int kProjPitch = kProjWMax + 8;  // 16-byte aligned rows with room for the 4-column alignment of the band
 constexpr int kProjMaxNa = 4;
 
 constexpr int kBpThreads = 256;
