@@ -71,7 +71,10 @@ struct Dadmm {
     int grid_proj = 0, grid_bp = 0;
     // workspace layout (byte offsets from the aligned base)
     size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_dual = 0,
-           off_res = 0, off_stats = 0, off_status = 0, ws_bytes = 0;
+           off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
+    // TMA descriptors of u and of its transposed copy (rebuilt with the graph)
+    CUtensorMap map_u{}, map_uT{};
+    int has_maps = 0;
     // stream / graph
     cudaStream_t own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -387,6 +390,7 @@ static void free_dadmm(Dadmm* h) {
 }
 
 struct WsPtrs {
+    float* uT;
     float* resid;
     int* counters;
     unsigned* lo;
@@ -401,6 +405,7 @@ struct WsPtrs {
 static WsPtrs ws_ptrs(const Dadmm& h, void* ws) {
     char* b = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     WsPtrs w;
+    w.uT = (float*)(b + h.off_uT);
     w.resid = (float*)(b + h.off_resid);
     w.counters = (int*)(b + h.off_counters);
     w.lo = (unsigned*)(b + h.off_lo);
@@ -459,6 +464,11 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     TOMO_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(long long) * SM, s));
 
     ProjParams pp{};
+    if (h.has_maps) {
+        pp.map = h.map_u;
+        pp.mapT = h.map_uT;
+        pp.has_map = pp.has_mapT = 1;
+    }
     pp.img = st.u;
     pp.out = w.resid;
     pp.sub = sino;
@@ -481,6 +491,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     bp.view.seg_of_row = h.d_seg_of_row;
     bp.view.eta1 = h.d_eta1;
     bp.view.u = st.u;
+    bp.view.uT = h.has_maps ? w.uT : nullptr;
     bp.view.lam = st.lam;
     bp.view.rho = (float)h.rho;
     bp.view.D = h.D;
@@ -789,6 +800,7 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                 return o;
             };
             const size_t SMn = (size_t)c.S * M;
+            h->off_uT = take(sizeof(float) * (size_t)c.S * M * N * N);
             h->off_resid = take(sizeof(float) * (size_t)c.S * A * c.n_bins);
             h->off_counters = take(sizeof(int) * (2 * (size_t)c.E1 + 2));
             h->off_lo = take(sizeof(unsigned) * SMn);
@@ -864,6 +876,16 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
             TOMO_CUDA(cudaStreamSynchronize(user));
             TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), user));
         }
+        // TMA descriptors of u and u^T; u^T is refreshed from u at every call (the state may
+        // have been set from outside), then kept in step by the u-step epilogue
+        const bool maps = make_image_map(&h.map_u, st->u, h.N, h.S * h.M) &&
+                          make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
+        if (maps != (h.has_maps != 0) && h.gexec) {
+            TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
+            h.gexec = nullptr;
+        }
+        h.has_maps = maps ? 1 : 0;
+        if (maps) launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
                                                   w.resid};

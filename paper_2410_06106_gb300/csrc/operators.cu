@@ -21,11 +21,14 @@
 // 2^-40 fixed point (int64) from the block origin, so that FP32 only ever
 // holds offsets below 64 pixels: the weight error stays at ~1e-6 even at
 // N = 2048 and for the steep ramps of near-axis angles.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+
+#include <cudaTypedefs.h>
 
 #include "tomo_internal.cuh"
 
@@ -208,20 +211,62 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ---- TMA (cp.async.bulk.tensor) and mbarrier helpers ---------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// one thread: arm the barrier for `bytes` and start the 3-D box load
+__device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar,
+                                             unsigned bytes) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            (unsigned)__cvta_generic_to_shared(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(b)
+        : "memory");
+}
+
+// bounded wait for the given phase of a barrier; false when the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(b), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------------
 // projector
 // ------------------------------------------------------------------
 
-// thread -> (angle slot, bin offset) of an item of na angles x 256/na bins.
-// na = 4: warp w takes bins 16 (w & 3) .. + 16 of angles 2 (w >> 2) and +1;
-// na = 2: warp w takes bins 16 w .. + 16 of both angles; na = 1: 32 bins.
-// Half-warps of adjacent angles read nearly the same shared words, so a
-// warp touches few banks twice.
-__device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& boff) {
+// thread -> (angle slot, bin offset, row group) of an item:
+// na = 4: 4 angles x 64 bins, warp w takes bins 16 (w & 3) .. + 16 of angles
+//         2 (w >> 2) and + 1 (half-warps of adjacent angles read nearly the
+//         same shared words);
+// na = 2: 2 angles x 128 bins, warp w takes bins 16 w .. + 16 of both;
+// na = 1: 128 bins x 2 row groups (threads 128..255 take rows 16..31 of
+//         every chunk; the two partial sums are added at the end).
+__device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& boff, int& rgrp) {
     const int lane = tid & 31, warp = tid >> 5;
+    rgrp = 0;
     if (na == 1) {
         slot = 0;
-        boff = tid;
+        boff = tid & 127;
+        rgrp = tid >> 7;
     } else if (na == 2) {
         slot = lane >> 4;
         boff = 16 * warp + (lane & 15);
@@ -231,13 +276,65 @@ __device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& b
     }
 }
 
-__global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams p) {
-    extern __shared__ __align__(16) float tile[];  // [kProjRows][kProjPitch]
+__device__ __forceinline__ int proj_bins(int na) { return na == 1 ? 128 : kProjThreads / na; }
+
+// NR consecutive rows of one ray inside a staged chunk: the two candidate
+// pixels of each row, weighted by the trapezoid (see the file header)
+template <int NR>
+__device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjAngle& A) {
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int pl = f0 + r * A.dm25;  // position - J at this row (2^-25), may be negative
+        const float F = one_plus_frac25(pl);
+        const float* t = base + r * kProjPitch + (pl >> kFracBits);  // lower candidate pixel
+        const float w0 = __saturatef(fmaf(-A.kappa, F, A.wf0));
+        const float w1 = __saturatef(fmaf(A.kappa, F, A.wf1));
+        acc = fmaf(w0, t[0], acc);
+        acc = fmaf(w1, t[1], acc);
+    }
+    return acc;
+}
+
+// staged minor range of chunk m0 of the item: extremes over its corner rays
+// (warp 0; lane 0 returns q0, the first staged column, 16-byte aligned)
+__device__ __forceinline__ int proj_chunk_q0(const ProjAngle* sa, int na, int b0, int blast, int m0, int lane,
+                                             int* w_out) {
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    if (lane < 4 * na) {
+        const ProjAngle& C = sa[lane >> 2];
+        const int bb = (lane & 1) ? blast : b0;
+        const int mm = (lane & 2) ? m0 + kProjRows - 1 : m0;
+        lo = hi = (long long)bb * C.Db + (long long)mm * C.Dm + C.K0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int q0 = ((int)(lo >> 40) - 2) & ~3;
+    *w_out = (int)(hi >> 40) + 3 - q0;
+    return q0;
+}
+
+__global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_constant__ ProjParams p) {
+    extern __shared__ __align__(1024) unsigned char proj_dyn[];
+    float* stage = reinterpret_cast<float*>(proj_dyn);  // [2][kProjRows][kProjPitch]
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ ProjAngle sa[kProjMaxNa];
-    __shared__ int s_item, s_q0, s_w;
+    __shared__ int s_item, s_q0[2], s_bad;
+    __shared__ float s_part[kProjThreads / 2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, B = p.B;
     const size_t n = (size_t)N * N;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+        s_bad = 0;
+    }
+    __syncthreads();
+    unsigned uses0 = 0, uses1 = 0;  // completed loads per stage: the parity to wait for
 
     for (int pass = 0;; ++pass) {
         int it;
@@ -248,116 +345,130 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const ProjParams 
         } else {
             it = pass == 0 ? (int)blockIdx.x : p.n_items;
         }
-        if (it >= p.n_items) break;
+        if (it >= p.n_items || s_bad) break;
         const ProjItem item = p.items[it];
         if (tid < item.na) sa[tid] = proj_angle(N, B, c_trig[p.const_off + p.angs[item.ang0 + tid].angle]);
         __syncthreads();
 
-        const int na = item.na, wb = kProjThreads / na;
-        int slot, boff;
-        proj_lane_map(na, tid, slot, boff);
+        const int na = item.na;
+        int slot, boff, rgrp;
+        proj_lane_map(na, tid, slot, boff, rgrp);
         const int b = item.b0 + boff;
-        const int blast = min(item.b0 + wb - 1, B - 1);
+        const int blast = min(item.b0 + proj_bins(na) - 1, B - 1);
         const int bc = min(b, blast);  // rays past the last bin shadow it (their output is dropped)
         const ProjAngle A = sa[slot];
         const int colmaj = sa[0].colmaj;
+        const bool tma = colmaj ? p.has_mapT : p.has_map;
+        const CUtensorMap* map = colmaj ? &p.mapT : &p.map;
         const float* img = p.img + (size_t)item.img * n;
-        long long pos = (long long)bc * A.Db + (long long)item.m_lo * A.Dm + A.K0;  // at the first chunk
+        // this ray's position at the first row of its row group in chunk 0
+        const int r0 = rgrp * (kProjRows / 2);
+        long long pos = (long long)bc * A.Db + (long long)(item.m_lo + r0) * A.Dm + A.K0;
         const long long dpos = (long long)kProjRows * A.Dm;
+        const int nch = item.nchunks;
         float total = 0.f;
 
-        for (int ch = 0; ch < item.nchunks; ++ch, pos += dpos) {
+        if (warp == 0 && nch > 0) {  // chunk 0: range, and its load when TMA is available
+            int w;
+            const int q0 = proj_chunk_q0(sa, na, item.b0, blast, item.m_lo, lane, &w);
+            if (lane == 0) {
+                s_q0[0] = q0;
+                if (w > kProjWMax + 3) atomicOr(&s_bad, 1);  // unreachable: the host bounds the extent
+                if (tma) {
+                    fence_proxy_async();
+                    tma_load_box(stage, map, q0, item.m_lo, item.img, &bars[0], 4 * kProjStageFloats);
+                }
+            }
+        }
+        for (int ch = 0; ch < nch; ++ch, pos += dpos) {
+            const int sb = ch & 1;
+            float* tile = stage + sb * kProjStageFloats;
             const int m0 = item.m_lo + ch * kProjRows;
-            if (warp == 0) {  // staged minor range: extremes over the item's corner rays
-                long long lo = LLONG_MAX, hi = LLONG_MIN;
-                if (lane < 4 * na) {
-                    const ProjAngle& C = sa[lane >> 2];
-                    const int bb = (lane & 1) ? blast : item.b0;
-                    const int mm = (lane & 2) ? m0 + kProjRows - 1 : m0;
-                    lo = hi = (long long)bb * C.Db + (long long)mm * C.Dm + C.K0;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-                }
+            __syncthreads();  // chunk ch-1 consumed by every thread; s_q0[sb] visible
+            if (s_bad) break;
+            if (warp == 0 && ch + 1 < nch) {  // next chunk: range and (TMA) load into the other stage
+                int w;
+                const int q1 = proj_chunk_q0(sa, na, item.b0, blast, m0 + kProjRows, lane, &w);
                 if (lane == 0) {
-                    const int q0 = (int)(lo >> 40) - 2;
-                    s_q0 = q0;
-                    s_w = (int)(hi >> 40) + 3 - q0;
+                    s_q0[sb ^ 1] = q1;
+                    if (w > kProjWMax + 3) atomicOr(&s_bad, 1);
+                    if (tma) {
+                        fence_proxy_async();
+                        tma_load_box(stage + (sb ^ 1) * kProjStageFloats, map, q1, m0 + kProjRows, item.img,
+                                     &bars[sb ^ 1], 4 * kProjStageFloats);
+                    }
                 }
             }
-            __syncthreads();  // previous chunk fully consumed; s_q0/s_w visible
-            int q0 = s_q0;
-            const int w = s_w;
-            if (w > kProjWMax) {  // unreachable: the host bounds every item's extent
-                if (tid == 0 && p.status) atomicOr(p.status, 1);
-                __syncthreads();  // every thread has read s_q0 / s_w
-                continue;
-            }
-            // stage the band the item's rays cross (zero outside the image), asynchronously
-            if (!colmaj) {
-                // rows: the band starts at a multiple of 4 columns so that whole
-                // 16-byte groups inside the image are copied at once
-                q0 &= ~3;
-                const int ng = (s_q0 + w - q0 + 3) >> 2;  // 16-byte groups per row (<= kProjPitch / 4)
-                const bool vec = (N & 3) == 0;
-                for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
-                    const int row = m0 + r;
-                    const bool rok = (unsigned)row < (unsigned)N;
-                    const float* src = img + (size_t)(rok ? row : 0) * N;
-                    float* dst = tile + r * kProjPitch;
-                    for (int g = lane; g < ng; g += 32) {
-                        const int col = q0 + 4 * g;
-                        if (vec && rok && col >= 0 && col + 4 <= N) {
-                            cp_async16(dst + 4 * g, src + col);
-                        } else {
+            const int q0 = s_q0[sb];
+            if (tma) {
+                const unsigned ph = sb ? (uses1++ & 1u) : (uses0++ & 1u);
+                if (!mbar_wait(&bars[sb], ph)) {  // a load that never lands: give up on the launch
+                    if (p.status) atomicOr(p.status, 4);
+                    atomicOr(&s_bad, 1);
+                }
+            } else {
+                // cp.async staging of the band (zero outside the image)
+                if (!colmaj) {
+                    const int ng = kProjPitch / 4;
+                    const bool vec = (N & 3) == 0;
+                    for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
+                        const int row = m0 + r;
+                        const bool rok = (unsigned)row < (unsigned)N;
+                        const float* src = img + (size_t)(rok ? row : 0) * N;
+                        float* dst = tile + r * kProjPitch;
+                        for (int g = lane; g < ng; g += 32) {
+                            const int col = q0 + 4 * g;
+                            if (vec && rok && col >= 0 && col + 4 <= N) {
+                                cp_async16(dst + 4 * g, src + col);
+                            } else {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const bool ok = rok && (unsigned)(col + e) < (unsigned)N;
-                                cp_async4(dst + 4 * g + e, ok ? src + col + e : img, ok);
+                                for (int e = 0; e < 4; ++e) {
+                                    const bool ok = rok && (unsigned)(col + e) < (unsigned)N;
+                                    cp_async4(dst + 4 * g + e, ok ? src + col + e : img, ok);
+                                }
                             }
                         }
                     }
+                } else {
+                    const int col = m0 + lane;
+                    const bool cok = (unsigned)col < (unsigned)N;
+                    for (int q = warp; q < kProjPitch; q += kProjThreads / 32) {
+                        const int row = q0 + q;
+                        const bool ok = cok && (unsigned)row < (unsigned)N;
+                        cp_async4(tile + lane * kProjPitch + q, ok ? img + (size_t)row * N + col : img, ok);
+                    }
                 }
-            } else {
-                const int col = m0 + lane;
-                const bool cok = (unsigned)col < (unsigned)N;
-                for (int q = warp; q < w; q += kProjThreads / 32) {
-                    const int row = q0 + q;
-                    const bool ok = cok && (unsigned)row < (unsigned)N;
-                    cp_async4(tile + lane * kProjPitch + q, ok ? img + (size_t)row * N + col : img, ok);
-                }
+                cp_async_wait_all();
+                __syncthreads();
             }
-            cp_async_wait_all();
-            __syncthreads();
-
-            // this ray: integer part J and 2^-25 fraction of its position at row m0
+            if (s_bad) continue;  // skip the compute; the loop top exits
+            // this ray: integer part J and 2^-25 fraction of its position at its first row
             const int J = (int)(pos >> 40);
             const int f0 = (int)((pos >> 15) & 0x1FFFFFF);
-            const float* base = tile + (J - q0);
-            float acc = 0.f;
-#pragma unroll
-            for (int r = 0; r < kProjRows; ++r) {
-                const int pl = f0 + r * A.dm25;  // position - J at row m0 + r (2^-25), may be negative
-                const float F = one_plus_frac25(pl);
-                const float* t = base + r * kProjPitch + (pl >> kFracBits);  // lower candidate pixel
-                const float w0 = __saturatef(fmaf(-A.kappa, F, A.wf0));
-                const float w1 = __saturatef(fmaf(A.kappa, F, A.wf1));
-                acc = fmaf(w0, t[0], acc);
-                acc = fmaf(w1, t[1], acc);
-            }
-            total += acc;
+            const float* base = tile + r0 * kProjPitch + (J - q0);
+            total += (na == 1) ? ray_rows<kProjRows / 2>(base, f0, A) : ray_rows<kProjRows>(base, f0, A);
         }
-
-        if (b < B) {
+        if (s_bad) {  // wait (bounded) for a load still in flight before leaving
+            if (tid == 0 && tma) {
+                mbar_wait(&bars[0], uses0 & 1u);
+                mbar_wait(&bars[1], uses1 & 1u);
+            }
+            break;
+        }
+        if (na == 1) {  // add the second row group's partial sums, in a fixed order
+            __syncthreads();
+            if (rgrp) s_part[tid & 127] = total;
+            __syncthreads();
+            if (!rgrp) total += s_part[tid];
+        }
+        if (b < B && !rgrp) {
             const AngRow ar = p.angs[item.ang0 + slot];
             const size_t o = ((size_t)item.outb + ar.row) * B + b;
             float v = A.h * total;
             if (p.sub) v -= __ldg(p.sub + o);
             p.out[o] = v;
         }
-        __syncthreads();  // sa / s_item reused by the next item
+        __syncthreads();  // sa / s_item / s_q0 reused by the next item
     }
 }
 
@@ -504,14 +615,89 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     const float uo = u[o];
                     const float x = xv ? xv[col] : 0.f;
                     const float g = acc[ky][kx] + V.rho * (uo - x) + lam[o];
-                    u[o] = uo - eta * g;
+                    acc[ky][kx] = uo - eta * g;
+                    u[o] = acc[ky][kx];
                 }
+            }
+            if (V.uT) {  // the transposed copy read by the projector's steep-ray items
+                float* T = reinterpret_cast<float*>(win);  // 64 x 65 floats, free after the angle loop
+#pragma unroll
+                for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 16 * ky] = acc[ky][kx];
+                __syncthreads();
+                float* ut = V.uT + (size_t)item.img * n;
+#pragma unroll
+                for (int i = 0; i < kBpTileX * kBpTileY / kBpThreads; ++i) {
+                    const int e = tid + i * kBpThreads;
+                    const int cc = e >> 6, rr = e & 63;
+                    if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
+                }
+                __syncthreads();  // the window buffer is reused by the next item
             }
         }
     }
 }
 
-static size_t proj_smem() { return sizeof(float) * kProjRows * kProjPitch; }
+// out[k][j][i] = in[k][i][j] for nimg images of N x N
+__global__ void transpose_kernel(const float* in, float* out, int N, int nimg) {
+    __shared__ float t[32][33];
+    const int tiles = (N + 31) / 32;
+    for (long long b = blockIdx.x; b < (long long)nimg * tiles * tiles; b += gridDim.x) {
+        const int k = (int)(b / ((long long)tiles * tiles));
+        const int rem = (int)(b - (long long)k * tiles * tiles);
+        const int ti = rem / tiles, tj = rem - ti * tiles;
+        const float* src = in + (size_t)k * N * N;
+        float* dst = out + (size_t)k * N * N;
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = ti * 32 + r, j = tj * 32 + threadIdx.x;
+            if (i < N && j < N) t[r][threadIdx.x] = src[(size_t)i * N + j];
+        }
+        __syncthreads();
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int j = tj * 32 + r, i = ti * 32 + threadIdx.x;
+            if (i < N && j < N) dst[(size_t)j * N + i] = t[threadIdx.x][r];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st) {
+    const long long tiles = (long long)nimg * ((N + 31) / 32) * ((N + 31) / 32);
+    transpose_kernel<<<(int)std::min<long long>(tiles, 152 * 16), dim3(32, 8), 0, st>>>(in, out, N, nimg);
+    TOMO_CUDA(cudaGetLastError());
+}
+
+// ---- TMA descriptors -------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg) {
+    std::memset(map, 0, sizeof(*map));
+    const auto fn = tensor_map_encoder();
+    if (!fn || ((uintptr_t)base & 15) || (N & 3) || nimg < 1) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)nimg};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * 4, (cuuint64_t)N * N * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kProjPitch, (cuuint32_t)kProjRows, 1};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static size_t proj_smem() { return sizeof(float) * 2 * kProjStageFloats; }
 
 // the dynamic shared-memory opt-in, set once per process before any capture
 static void ensure_proj_attr() {
@@ -647,7 +833,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
             // extent check over every bin run and chunk
             std::vector<HostProj> As;
             for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-            const int wb = kProjThreads / na;
+            const int wb = na == 1 ? 128 : kProjThreads / na;
             bool ok = true;
             for (int b0 = 0; b0 < g.B && ok; b0 += wb) {
                 const int b1 = std::min(b0 + wb - 1, g.B - 1);
@@ -670,7 +856,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
                                            std::to_string(angs[i].angle) + ")");
         std::vector<HostProj> As;
         for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-        const int wb = kProjThreads / na;
+        const int wb = na == 1 ? 128 : kProjThreads / na;
         for (int b0 = 0; b0 < g.B; b0 += wb) {
             const int b1 = std::min(b0 + wb - 1, g.B - 1);
             int lo = g.N, hi = -1;
@@ -901,6 +1087,8 @@ tomo_status tomo_project(tomo_geometry_t gh, const float* img, float* sino, cons
         TOMO_REQUIRE(angle_idx || n_sel == g->A, "angle_idx NULL requires n_sel == n_angles");
         Geometry::Sel& s = selection(*g, angle_idx, n_sel, batch);
         ProjParams p{};
+        p.has_map = make_image_map(&p.map, img, g->N, batch) ? 1 : 0;
+        p.has_mapT = 0;
         p.img = img;
         p.out = sino;
         p.sub = subtract;

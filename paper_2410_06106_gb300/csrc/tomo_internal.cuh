@@ -2,6 +2,7 @@
 // Everything here is library-private; the public ABI is include/tomo.h.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (TMA descriptors); the driver entry point is fetched at run time
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -96,10 +97,11 @@ struct BpItem {
 };
 
 constexpr int kProjThreads = 256;
-constexpr int kProjRows = 32;   // rows per staged chunk
-constexpr int kProjWMax = 400;  // max staged minor extent (256 bins at 45 degrees need 399)
-constexpr int kProjPitch = kProjWMax + 8;  // 16-byte aligned rows with room for the 4-column alignment of the band
+constexpr int kProjRows = 32;    // rows per staged chunk (the TMA box height)
+constexpr int kProjPitch = 256;  // staged columns per row (the TMA box width)
+constexpr int kProjWMax = 252;   // max staged minor extent; + 3 for the 16-byte aligned start
 constexpr int kProjMaxNa = 4;
+constexpr int kProjStageFloats = kProjRows * kProjPitch;  // one 32 KB stage; two stages in flight
 
 constexpr int kBpThreads = 256;
 constexpr int kBpTileX = 64, kBpTileY = 64;
@@ -137,8 +139,13 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
 void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb,
                     int node, int slice, std::vector<BpItem>& out);
 
-// launch parameters
+// launch parameters. map / mapT: TMA descriptors of the images [nimg][N][N]
+// and of their transposes; items of steep rays (columns major) read mapT,
+// the others map. Without a descriptor an item stages its band with
+// cp.async instead.
 struct ProjParams {
+    CUtensorMap map;
+    CUtensorMap mapT;
     const float* img;
     float* out;
     const float* sub;  // may be null
@@ -148,7 +155,12 @@ struct ProjParams {
     int* status;   // device error word (may be null)
     int n_items;
     int N, B, const_off;
+    int has_map, has_mapT;
 };
+
+// TMA descriptor of nimg images [N][N] float32 at base with a 32 x 256 box;
+// false when the layout cannot be described (unaligned base, N % 4 != 0)
+bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg);
 
 struct BpView {  // dADMM epilogue: where every node's view of x lives
     const float* hist;        // [D][3][S][N][N]
@@ -158,6 +170,7 @@ struct BpView {  // dADMM epilogue: where every node's view of x lives
     const int32_t* seg_of_row;  // [N]
     const float* eta1;        // [M]
     float* u;                 // [S][M][N][N]
+    float* uT;                // [S][M][N][N] transposed copy kept in step with u (may be null)
     const float* lam;         // [S][M][N][N]
     float rho;
     int D, S, M;
@@ -177,6 +190,7 @@ struct BpParams {
 };
 
 void launch_project(const ProjParams& p, int grid, cudaStream_t st);
+void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st);
 void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st);
 void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st);
 int persistent_grid_project();
