@@ -132,6 +132,23 @@ TOMO_API tomo_status tomo_opnorm_sq(tomo_geometry_t g, const int32_t* angle_idx,
                            tomo_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Elementwise building blocks of the differentiable unrolled ADMM      */
+/* (Algorithm 2 step, Algorithm 3 closed form, Eq. 18; their adjoints)  */
+/* ------------------------------------------------------------------ */
+
+/* out[i] = sum_{j<k} coef[j] * x[j][i], i < n. x: HOST array of k device
+ * pointers (float32, n each); coef: HOST array of k floats; 1 <= k <= 4.
+ * out may alias any x[j] (every element is read before it is written). */
+TOMO_API tomo_status tomo_lincomb(int64_t n, int k, const float* const* x, const float* coef, float* out,
+                                  tomo_stream_t stream);
+
+/* FP64 dot product sum_i x[i] y[i] (fixed reduction order: deterministic).
+ * out: DEVICE float64 array of at least TOMO_DOT_SCRATCH entries; out[0]
+ * receives the result, the rest is scratch. */
+#define TOMO_DOT_SCRATCH 257
+TOMO_API tomo_status tomo_dot(int64_t n, const float* x, const float* y, double* out, tomo_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Message quantizers (Sec. 2.7)                                       */
 /* ------------------------------------------------------------------ */
 

@@ -75,6 +75,8 @@ SIGNATURES = {
     "dadmm_step": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_int, C.c_void_p,
                              C.c_size_t, C.c_void_p, C.c_void_p]),
     "dadmm_home_view": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_void_p]),
+    "tomo_lincomb": (C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tomo_dot": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dadmm_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "dadmm_num_phases": (C.c_int, [C.c_void_p]),
     "dadmm_phase_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -236,6 +238,31 @@ def quant_jpeg(x, quality):
     _check(lib().quant_jpeg(_ptr(x), rows, cols, int(quality), _ptr(coefs), _ptr(lohi), _ptr(deq), _ptr(nnz),
                             _stream()))
     return coefs, lohi, deq, nnz
+
+
+def lincomb(xs, coefs, out=None):
+    """out = sum_j coefs[j] * xs[j] (CUDA float32 tensors of equal size, 1..4 terms)"""
+    _require_cuda(*xs)
+    k = len(xs)
+    n = xs[0].numel()
+    for t in xs:
+        assert t.numel() == n
+    if out is None:
+        out = torch.empty_like(xs[0])
+    ptrs = (C.c_void_p * k)(*[t.data_ptr() for t in xs])
+    cf = (C.c_float * k)(*[float(c) for c in coefs])
+    _check(lib().tomo_lincomb(n, k, ptrs, cf, _ptr(out), _stream()))
+    return out
+
+
+def dot(x, y, scratch=None):
+    """FP64 dot product of two CUDA float32 tensors, as a 0-dim CUDA float64 tensor"""
+    _require_cuda(x, y)
+    assert x.numel() == y.numel()
+    if scratch is None:
+        scratch = torch.empty(257, dtype=torch.float64, device=x.device)
+    _check(lib().tomo_dot(x.numel(), _ptr(x), _ptr(y), _ptr(scratch), _stream()))
+    return scratch[0]
 
 
 class DADMM:

@@ -337,6 +337,51 @@ __global__ void home_view_kernel(const float* hist, const int32_t* iter, const i
 }
 
 // ------------------------------------------------------------------
+// elementwise building blocks (linear combinations, FP64 dots)
+// ------------------------------------------------------------------
+struct LinComb {
+    const float* x[4];
+    float c[4];
+};
+
+template <int K>
+__global__ void lincomb_kernel(const LinComb a, float* out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v = a.c[0] * a.x[0][i];
+#pragma unroll
+        for (int j = 1; j < K; ++j) v = fmaf(a.c[j], a.x[j][i], v);
+        out[i] = v;
+    }
+}
+
+constexpr int kDotBlocks = TOMO_DOT_SCRATCH - 1;
+
+__global__ void dot_partial_kernel(const float* x, const float* y, long long n, double* part) {
+    __shared__ double s[kElemThreads / 32];
+    double acc = 0.0;
+    for (long long base = (long long)blockIdx.x * kElemThreads; base < n; base += (long long)kDotBlocks * kElemThreads) {
+        const long long i = base + threadIdx.x;
+        if (i < n) acc = fma((double)x[i], (double)y[i], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kElemThreads / 32; ++w) t += s[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void dot_final_kernel(const double* part, double* out) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < kDotBlocks; ++b) t += part[b];
+        *out = t;
+    }
+}
+
+// ------------------------------------------------------------------
 // host
 // ------------------------------------------------------------------
 static void relay_tables(int M, const std::vector<int32_t>& adj, std::vector<int>& dist,
@@ -610,6 +655,39 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
 using namespace tomo;
 
 extern "C" {
+
+tomo_status tomo_lincomb(int64_t n, int k, const float* const* x, const float* coef, float* out,
+                         tomo_stream_t stream) {
+    return guard([&] {
+        TOMO_REQUIRE(n >= 0 && k >= 1 && k <= 4 && x && coef && out, "bad tomo_lincomb arguments");
+        LinComb a{};
+        for (int j = 0; j < k; ++j) {
+            TOMO_REQUIRE(x[j] != nullptr, "tomo_lincomb: NULL input");
+            a.x[j] = x[j];
+            a.c[j] = coef[j];
+        }
+        if (n == 0) return;
+        const int grid = (int)std::min<long long>((n + kElemThreads - 1) / kElemThreads, 152LL * 16);
+        cudaStream_t s = (cudaStream_t)stream;
+        switch (k) {
+            case 1: lincomb_kernel<1><<<grid, kElemThreads, 0, s>>>(a, out, n); break;
+            case 2: lincomb_kernel<2><<<grid, kElemThreads, 0, s>>>(a, out, n); break;
+            case 3: lincomb_kernel<3><<<grid, kElemThreads, 0, s>>>(a, out, n); break;
+            default: lincomb_kernel<4><<<grid, kElemThreads, 0, s>>>(a, out, n); break;
+        }
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
+
+tomo_status tomo_dot(int64_t n, const float* x, const float* y, double* out, tomo_stream_t stream) {
+    return guard([&] {
+        TOMO_REQUIRE(n >= 0 && x && y && out, "bad tomo_dot arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        dot_partial_kernel<<<kDotBlocks, kElemThreads, 0, s>>>(x, y, n, out + 1);
+        dot_final_kernel<<<1, 32, 0, s>>>(out + 1, out);
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
 
 tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* out) {
     return guard([&] {

@@ -1,0 +1,126 @@
+"""Differentiation: the projector as a torch.autograd.Function (backward = the
+matched backprojection kernel) and the unrolled 10-iteration unquantized
+dADMM, differentiated with respect to rho and the sinogram with one
+checkpoint per iteration. Checked against central finite differences of the
+FP64 oracle (small problem) and of the GPU forward (full 1024^2 size), and
+against the oracle's adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_common import cuda, need_gpu, rel_l2
+from paper_2410_06106_gb300 import api, autograd, synth
+from problems import oracle_eta1, small_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def test_project_function_adjoint_on_64_directions_full_size():
+    """C4 geometry (1024^2, 1440 angles, 1449 bins): <w, P v> by central
+    differences of the forward equals <P^T w, v> from autograd for 64 seeded
+    directions; the autograd gradient equals the oracle's P^T w at sampled
+    pixels"""
+    need_gpu()
+    cfg = synth.CONFIGS["c4_diff"]
+    N, A, B = cfg["N"], cfg["A"], cfg["B"]
+    theta = synth.angles(A)
+    g = api.Geometry(N, B, theta)
+    rng = np.random.default_rng(4)
+    u0 = cuda(rng.random((N, N)))
+    w = cuda(rng.standard_normal((A, B)))
+    u = u0.clone().requires_grad_(True)
+    y = autograd.project(u, g)
+    (y * w).sum().backward()
+    grad = u.grad.detach()
+    errs = []
+    for k in range(64):
+        v = cuda(np.random.default_rng(100 + k).standard_normal((N, N)))
+        fd = (torch.sum(g.project(u0 + v).double() * w.double()) - torch.sum(g.project(u0 - v).double() * w.double())) / 2
+        ad = torch.sum(grad.double() * v.double())
+        errs.append(abs(fd.item() - ad.item()) / abs(ad.item()))
+    assert max(errs) <= 1e-4, max(errs)
+    og = O.Geometry(N, B, theta)
+    pix = rng.integers(0, N * N, 64)
+    ref = og.backproject_pixels(w.cpu().numpy(), pix)
+    assert rel_l2(grad.cpu().numpy().ravel()[pix], ref) <= 1e-5
+    g.close()
+
+
+def oracle_x(p, eta, rho, sino):
+    o = O.DADMM(dict(p, rho=rho), eta)
+    for _ in range(10):
+        o.iterate(sino)
+    return o.home_view()[0]
+
+
+def oracle_loss(p, eta, w, rho, sino):
+    return float(np.sum(w * oracle_x(p, eta, rho, sino)))
+
+
+def test_unrolled_admm_gradients_match_oracle_finite_differences():
+    need_gpu()
+    N, A, B, M = 32, 48, 47, 8
+    p = small_problem(N=N, A=A, B=B, M=M, graph="complete", part="interleaved", noise=0.01, seed=9,
+                      E1=10, E2=10, rho=1.0, eta2=0.2)
+    eta = oracle_eta1(p, iters=60)
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal((N, N))
+    sino = p["sino"][0]
+    g = api.Geometry(N, B, p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    sel = [idx[ptr[m]:ptr[m + 1]] for m in range(M)]
+    rho = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    d = cuda(sino).requires_grad_(True)
+    x = autograd.unrolled_admm(d, g, sel, p["seg_row_ptr"], rho, eta, eta2=0.2, E1=10, E2=10, iters=10)
+    loss = torch.sum(x.double() * cuda(w).double())
+    loss.backward()
+    # forward parity with the oracle (10 unquantized iterations, complete graph)
+    assert rel_l2(x.detach().cpu().numpy(), oracle_x(p, eta, 1.0, sino[None])) <= 1e-4
+    # d L / d rho (eta1 fixed) by central differences of the FP64 oracle
+    h = 1e-3
+    fd_rho = (oracle_loss(p, eta, w, 1.0 + h, sino[None]) - oracle_loss(p, eta, w, 1.0 - h, sino[None])) / (2 * h)
+    assert abs(rho.grad.item() - fd_rho) <= 1e-3 * abs(fd_rho), (rho.grad.item(), fd_rho)
+    # directional derivative along a sinogram direction (the map is linear in d)
+    v = rng.standard_normal((A, B)).astype(np.float32)
+    fd_d = (oracle_loss(p, eta, w, 1.0, (sino + v)[None]) - oracle_loss(p, eta, w, 1.0, (sino - v)[None])) / 2
+    ad_d = float(torch.sum(d.grad.double() * cuda(v).double()))
+    assert abs(ad_d - fd_d) <= 1e-3 * abs(fd_d), (ad_d, fd_d)
+    g.close()
+
+
+def test_unrolled_admm_full_size_checkpointed():
+    """1024^2, 1440 angles, 8 nodes (interleaved, complete graph), 10 unrolled
+    iterations with per-iteration checkpoints: gradients against central
+    differences of the GPU forward"""
+    need_gpu()
+    prob = synth.make_problem("c4_diff")
+    gd = prob["geometry"]
+    g = api.Geometry(gd["N"], gd["B"], gd["theta"])
+    ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
+    sel = [idx[ptr[m]:ptr[m + 1]] for m in range(prob["M"])]
+    L = np.array([g.opnorm_sq(s, iters=20) for s in sel])
+    eta = 1.0 / (L + 1.0)
+    rng = np.random.default_rng(5)
+    w = cuda(rng.standard_normal((gd["N"], gd["N"])))
+    sino = cuda(prob["sino"][0])
+
+    def loss_of(rho_val, d, grad=False):
+        rho = torch.tensor(rho_val, dtype=torch.float64, requires_grad=grad)
+        x = autograd.unrolled_admm(d, g, sel, prob["seg_row_ptr"], rho, eta, iters=10, checkpoint=True)
+        return torch.sum(x.double() * w.double()), rho
+
+    torch.cuda.reset_peak_memory_stats()
+    d = sino.clone().requires_grad_(True)
+    loss, rho = loss_of(1.0, d, grad=True)
+    loss.backward()
+    h = 1e-2
+    with torch.no_grad():
+        fd = (loss_of(1.0 + h, sino)[0] - loss_of(1.0 - h, sino)[0]).item() / (2 * h)
+    assert abs(rho.grad.item() - fd) <= 1e-3 * abs(fd), (rho.grad.item(), fd)
+    v = torch.randn(sino.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    with torch.no_grad():
+        fdd = (loss_of(1.0, sino + v)[0] - loss_of(1.0, sino - v)[0]).item() / 2
+    add = float(torch.sum(d.grad.double() * v.double()))
+    assert abs(add - fdd) <= 1e-3 * abs(fdd), (add, fdd)
+    g.close()
