@@ -50,7 +50,7 @@ typedef int tomo_status;
 #define TOMO_ERR_INVALID_ARG -1 /* bad argument, nothing launched */
 #define TOMO_ERR_CUDA -2        /* a CUDA runtime call failed */
 #define TOMO_ERR_WORKSPACE -3   /* workspace / constant table too small */
-#define TOMO_ERR_TIMEOUT -4     /* reserved: a bounded device wait gave up */
+#define TOMO_ERR_TIMEOUT -4     /* a bounded device wait gave up (see *_sync_status) */
 #define TOMO_ERR_NUMERIC -5     /* non-finite values reached the statistics */
 
 /* Message of the calling thread's most recent error ("" if none). The string
@@ -71,11 +71,10 @@ typedef struct tomo_geometry* tomo_geometry_t;
  * radians, or NULL for theta_a = a pi / n_angles (uniform on [0, pi)).
  * Angles within 1e-12 rad of a multiple of pi/2 are snapped so that their
  * cosine and sine are exactly 0 or +-1.
- * The per-angle trig table is copied into the current device's constant
- * memory (a pool of TOMO_MAX_CONST_ANGLES angles shared by all live
- * geometries of the process); TOMO_ERR_WORKSPACE if the pool is full.
+ * The per-angle operator constants (fixed-point ray and pixel steps, trapezoid
+ * weight constants) are derived on the host in FP64 and copied into device
+ * tables owned by the geometry, on the current device.
  * Limits: 1 <= N <= 8192, 1 <= n_bins <= 16384, 1 <= n_angles <= 4096. */
-#define TOMO_MAX_CONST_ANGLES 3584
 TOMO_API tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* angles_rad,
                                  tomo_geometry_t* out);
 TOMO_API tomo_status tomo_geometry_destroy(tomo_geometry_t g);
@@ -130,6 +129,25 @@ TOMO_API size_t tomo_opnorm_workspace_size(tomo_geometry_t g, int n_sel);
 TOMO_API tomo_status tomo_opnorm_sq(tomo_geometry_t g, const int32_t* angle_idx, int n_sel, int iters,
                            uint64_t seed, void* work, size_t work_bytes, double* out,
                            tomo_stream_t stream);
+
+/* Device status of the standalone operator calls of geometry g
+ * (tomo_project, tomo_project_noalloc and the projections inside
+ * tomo_opnorm_sq): enqueues a read and a reset of g's status word on
+ * `stream`, synchronizes the stream and returns TOMO_ERR_TIMEOUT if a
+ * projector block stopped waiting for a staged image band (its bounded wait
+ * gave up; those outputs are incomplete), TOMO_ERR_CUDA on an internal
+ * staging-extent error, else TOMO_OK. Operator calls themselves are
+ * asynchronous and cannot report device-side failures; the word is shared by
+ * every call on g since the previous read. */
+TOMO_API tomo_status tomo_sync_status(tomo_geometry_t g, tomo_stream_t stream);
+
+/* Self test of the failure detection above, with no fault: launches one
+ * block that waits, with the projector's bounded wait, on a barrier that
+ * nothing completes; after timeout_ms (1..2000) of GPU time it sets the
+ * timeout bit of g's status word and returns, leaving the context usable.
+ * The next tomo_sync_status(g) returns TOMO_ERR_TIMEOUT. The projector's
+ * own waits give up after one second. */
+TOMO_API tomo_status tomo_selftest_wait(tomo_geometry_t g, int timeout_ms, tomo_stream_t stream);
 
 /* ------------------------------------------------------------------ */
 /* Elementwise building blocks of the differentiable unrolled ADMM      */
@@ -276,11 +294,20 @@ TOMO_API size_t dadmm_workspace_size(dadmm_t h);
  * BATCHED mode captures one iteration as a CUDA graph (re-captured when the
  * state/workspace/sino pointers or the stream change) and replays it.
  * stats: HOST [n_iters][S][DADMM_NSTAT] or NULL; when non-NULL the call
- * synchronizes the stream and fills it. Returns TOMO_ERR_NUMERIC if a
- * statistic is not finite (the state is still advanced). */
+ * synchronizes the stream, fills it and checks the device status word:
+ * TOMO_ERR_NUMERIC if a statistic is not finite (the state is still
+ * advanced), TOMO_ERR_TIMEOUT if a bounded device wait gave up. */
 TOMO_API tomo_status dadmm_step(dadmm_t h, const dadmm_state* st, const float* sino, int n_iters,
                        void* workspace, size_t workspace_bytes, double* stats,
                        tomo_stream_t stream);
+
+/* Device status of the iterations run with this workspace since the last
+ * read (dadmm_step with stats reads and resets it itself): reads and resets
+ * the word on `stream`, synchronizes, and returns TOMO_ERR_TIMEOUT (a bounded
+ * device wait gave up; the iterate is incomplete), TOMO_ERR_NUMERIC
+ * (non-finite statistics), TOMO_ERR_CUDA (internal error) or TOMO_OK. */
+TOMO_API tomo_status dadmm_sync_status(dadmm_t h, void* workspace, size_t workspace_bytes,
+                                       tomo_stream_t stream);
 
 /* Per-phase timing of the iterations. When enabled, dadmm_step records a
  * CUDA event (timing enabled) before and after every phase launch of an

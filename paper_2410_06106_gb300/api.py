@@ -77,6 +77,9 @@ SIGNATURES = {
     "dadmm_home_view": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_void_p]),
     "tomo_lincomb": (C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tomo_dot": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tomo_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tomo_selftest_wait": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dadmm_sync_status": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dadmm_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "dadmm_num_phases": (C.c_int, [C.c_void_p]),
     "dadmm_phase_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -141,12 +144,7 @@ class Geometry:
         self._theta = th
         h = C.c_void_p()
         tp = th.ctypes.data_as(C.c_void_p) if th is not None else None
-        rc = lib().tomo_geometry_create(self.N, self.B, self.A, tp, C.byref(h))
-        if rc == -3:  # constant trig pool full: release unreachable geometries, retry once
-            import gc
-            gc.collect()
-            rc = lib().tomo_geometry_create(self.N, self.B, self.A, tp, C.byref(h))
-        _check(rc)
+        _check(lib().tomo_geometry_create(self.N, self.B, self.A, tp, C.byref(h)))
         self.handle = h
 
     def close(self):
@@ -196,6 +194,11 @@ class Geometry:
         _check(lib().tomo_backproject(self.handle, _ptr(sino), _ptr(out), p, n_sel, batch, float(beta),
                                       _stream()))
         return out
+
+    def sync_status(self):
+        """raise TomoError if a device-side failure was recorded by an operator
+        call on this geometry since the last check (synchronizes the stream)"""
+        _check(lib().tomo_sync_status(self.handle, _stream()))
 
     def opnorm_sq(self, angle_idx=None, iters=100, seed=1):
         """||P_sel||^2 by power iteration on the GPU"""
@@ -342,6 +345,11 @@ class DADMM:
                                 _ptr(self.workspace), self.ws_bytes,
                                 st.ctypes.data_as(C.c_void_p) if stats else None, _stream()))
         return st
+
+    def sync_status(self):
+        """raise TomoError if a device-side failure (bounded wait that gave up,
+        non-finite statistics) was recorded since the last check"""
+        _check(lib().dadmm_sync_status(self.handle, _ptr(self.workspace), self.ws_bytes, _stream()))
 
     def set_profiling(self, enable=True):
         _check(lib().dadmm_set_profiling(self.handle, int(bool(enable))))

@@ -63,6 +63,7 @@ struct Dadmm {
     int32_t* d_recv = nullptr;
     int32_t* d_home = nullptr;
     float* d_eta1 = nullptr;
+    float* d_mx = nullptr;  // [A] max(|cos|, |sin|) per angle: undoes the residual's prescale
     SegTask* d_km = nullptr;
     SegTask* d_jp = nullptr;
     int n_km = 0, n_jp = 0, max_jp_rows = 0;
@@ -232,14 +233,21 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
 }
 
 // sum of squared residuals (last inner step) per slice
-__global__ void __launch_bounds__(kElemThreads) resid_kernel(const float* resid, int A, int B, double* part) {
+// sum of squares of the residual lines; line a is stored as h_a r_a and
+// mx[a] = 1 / h_a = max(|cos|, |sin|) restores r_a
+__global__ void __launch_bounds__(kElemThreads) resid_kernel(const float* resid, const float* mx, int A, int B,
+                                                             double* part) {
     __shared__ double s_red[kElemThreads / 32];
     const int slice = blockIdx.y;
     double acc = 0.0;
     for (int a = blockIdx.x; a < A; a += kResPerSlice) {
         const float* r = resid + ((size_t)slice * A + a) * B;
+        const float m = mx[a];
         float t = 0.f;
-        for (int b = threadIdx.x; b < B; b += kElemThreads) t = fmaf(r[b], r[b], t);
+        for (int b = threadIdx.x; b < B; b += kElemThreads) {
+            const float v = r[b] * m;
+            t = fmaf(v, v, t);
+        }
         acc += t;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -428,7 +436,7 @@ static void free_dadmm(Dadmm* h) {
     if (h->own) cudaStreamDestroy(h->own);
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
     void* ptrs[] = {h->d_angs, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
-                    h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_km, h->d_jp};
+                    h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_mx, h->d_km, h->d_jp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -521,14 +529,16 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     pp.status = w.status;
     pp.N = h.N;
     pp.B = h.B;
-    pp.const_off = h.g->const_off;
+    pp.ptab = h.g->d_ptab;
+    pp.prescale = 1;  // the residual is stored as h_a r_a, the form the backprojector stages
     BpParams bp{};
     bp.sino = w.resid;
     bp.angs = h.d_angs;
+    bp.btab = h.g->d_btab;
     bp.status = w.status;
     bp.N = h.N;
     bp.B = h.B;
-    bp.const_off = h.g->const_off;
+    bp.prescaled = 1;
     bp.view.hist = st.hist;
     bp.view.iter = st.iter;
     bp.view.lag = h.d_lag;
@@ -630,7 +640,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
             }
     }
     mark();
-    resid_kernel<<<dim3(kResPerSlice, h.S), kElemThreads, 0, s>>>(w.resid, h.A, h.B, w.res);
+    resid_kernel<<<dim3(kResPerSlice, h.S), kElemThreads, 0, s>>>(w.resid, h.d_mx, h.A, h.B, w.res);
     TOMO_CUDA(cudaGetLastError());
     FinParams fp{};
     fp.dual_part = w.dual;
@@ -648,6 +658,14 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     finalize_kernel<<<1, 256, 0, s>>>(fp);
     TOMO_CUDA(cudaGetLastError());
     mark();  // end of the last phase
+}
+
+// device status word of a dADMM workspace: bit 0 projector extent (internal
+// error), bit 1 non-finite statistics, bit 2 a bounded wait gave up
+static void check_status_word(int status, tomo_status* numeric) {
+    if (status & 4) fail(TOMO_ERR_TIMEOUT, "a bounded wait for a staged image band gave up; the iterate is incomplete");
+    if (status & 1) fail(TOMO_ERR_CUDA, "projector staging extent exceeded (internal error)");
+    if (status & 2) *numeric = TOMO_ERR_NUMERIC;
 }
 
 }  // namespace tomo
@@ -845,6 +863,9 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             std::vector<float> eta(M);
             for (int m = 0; m < M; ++m) eta[m] = (float)c.eta1[m];
             h->d_eta1 = device_upload(eta);
+            std::vector<float> mx(g->A);
+            for (int a = 0; a < g->A; ++a) mx[a] = (float)std::fmax(std::fabs(g->c[a]), std::fabs(g->s[a]));
+            h->d_mx = device_upload(mx);
             // codec tasks, slice-major
             std::vector<SegTask> km, jp;
             h->km_index.assign((size_t)c.S * M, -1);
@@ -932,6 +953,28 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
     });
 }
 
+tomo_status dadmm_sync_status(dadmm_t hh, void* workspace, size_t workspace_bytes, tomo_stream_t stream) {
+    tomo_status numeric = TOMO_OK;
+    tomo_status rc = guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        check_device(*h.g);
+        TOMO_REQUIRE(workspace != nullptr && workspace_bytes >= h.ws_bytes,
+                     "workspace too small: need " + std::to_string(h.ws_bytes) + " bytes");
+        const WsPtrs w = ws_ptrs(h, workspace);
+        cudaStream_t st = (cudaStream_t)stream;
+        int status = 0;
+        TOMO_CUDA(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+        TOMO_CUDA(cudaStreamSynchronize(st));
+        check_status_word(status, &numeric);
+    });
+    if (rc == TOMO_OK && numeric != TOMO_OK) {
+        set_last_error("non-finite statistics");
+        return numeric;
+    }
+    return rc;
+}
+
 tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters, void* workspace,
                        size_t workspace_bytes, double* stats, tomo_stream_t stream) {
     tomo_status numeric = TOMO_OK;
@@ -1011,8 +1054,7 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
                 const int kk = k0 + it;
                 std::memcpy(stats + (size_t)it * per, ring.data() + (size_t)(kk % kStatsCap) * per, sizeof(double) * per);
             }
-            if (status & 1) fail(TOMO_ERR_CUDA, "projector staging extent exceeded (internal error)");
-            if (status & 2) numeric = TOMO_ERR_NUMERIC;
+            check_status_word(status, &numeric);
         }
     });
     if (rc == TOMO_OK && numeric != TOMO_OK) {

@@ -89,11 +89,12 @@ tomo_status tomo_project_noalloc(tomo_geometry_t gh, const float* img, float* si
         p.items = d_items;
         p.angs = d_angs;
         p.counter = nullptr;
-        p.status = nullptr;
+        p.status = g->d_status;
         p.n_items = (int)items.size();
         p.N = g->N;
         p.B = g->B;
-        p.const_off = g->const_off;
+        p.ptab = g->d_ptab;
+        p.prescale = 0;
         launch_project(p, p.n_items, st);
     });
 }

@@ -42,48 +42,6 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 void clear_last_error() { g_last_error.clear(); }
 void fail(tomo_status code, const std::string& msg) { throw Error{code, msg}; }
 
-// ------------------------------------------------------------------
-// constant trig pool: (cos, sin) of every angle of every live geometry
-// ------------------------------------------------------------------
-__constant__ double2 c_trig[TOMO_MAX_CONST_ANGLES];
-
-namespace {
-struct ConstPool {
-    std::mutex mu;
-    // per device: occupied slots
-    std::vector<std::vector<char>> used;
-};
-ConstPool& pool() {
-    static ConstPool p;
-    return p;
-}
-
-int pool_alloc(int device, int count) {
-    ConstPool& P = pool();
-    std::lock_guard<std::mutex> lk(P.mu);
-    if ((int)P.used.size() <= device) P.used.resize(device + 1);
-    auto& u = P.used[device];
-    if (u.empty()) u.assign(TOMO_MAX_CONST_ANGLES, 0);
-    int run = 0;
-    for (int i = 0; i < TOMO_MAX_CONST_ANGLES; ++i) {
-        run = u[i] ? 0 : run + 1;
-        if (run == count) {
-            int first = i - count + 1;
-            for (int k = first; k <= i; ++k) u[k] = 1;
-            return first;
-        }
-    }
-    return -1;
-}
-
-void pool_free(int device, int first, int count) {
-    ConstPool& P = pool();
-    std::lock_guard<std::mutex> lk(P.mu);
-    if (first < 0 || device >= (int)P.used.size()) return;
-    for (int k = first; k < first + count; ++k) P.used[device][k] = 0;
-}
-}  // namespace
-
 Geometry* as_geometry(tomo_geometry_t g) {
     TOMO_REQUIRE(g != nullptr, "geometry handle is NULL");
     return reinterpret_cast<Geometry*>(g);
@@ -97,17 +55,17 @@ void check_device(const Geometry& g) {
 }
 
 // ------------------------------------------------------------------
-// per-angle parameters, derived in FP64 from the constant table
+// per-angle parameters: derived on the host in FP64 (tables per geometry)
 // ------------------------------------------------------------------
 constexpr float kGammaCap = 1048576.0f;  // 2^20
-constexpr double kFix25 = 33554432.0;    // 2^25: fixed point of positions inside a block
 constexpr int kFracBits = 25;
+constexpr double kFix25 = (double)(1 << kFracBits);  // 2^25: fixed point of positions inside a block
 
 // 1 + (fraction of a 2^-25 fixed-point position) as a float in [1, 2): the
 // top 23 of the 25 fraction bits become the mantissa (exact for the
 // half-integer positions of axis-aligned rays)
 __device__ __forceinline__ float one_plus_frac25(int p) {
-    return __int_as_float(((p >> 2) & 0x7FFFFF) | 0x3F800000);
+    return __int_as_float(((p >> (kFracBits - 23)) & 0x7FFFFF) | 0x3F800000);
 }
 
 // Weights of the two candidate pixels/bins around a position with fraction
@@ -116,19 +74,11 @@ __device__ __forceinline__ float one_plus_frac25(int p) {
 //   w_lower = sat(wf0 - g F), w_upper = sat(wf1 + g F),
 //   wf0 = 0.5 + g (w_mid + 1), wf1 = 0.5 + g (w_mid - 2).
 
-struct ProjAngle {
-    long long Db, Dm, K0;  // minor coordinate of ray b at major index m: b Db + m Dm + K0 (2^-40)
-    int dm25;              // Dm in 2^-25, for stepping inside a chunk
-    float kappa;           // |major| / |minor|: the weight slope in minor-index units
-    float wf0, wf1;        // weight constants (w_mid = 1/2 in minor units)
-    float h;               // 1 / |major|
-    int colmaj;            // 0: image rows are the major axis; 1: columns
-};
-
-__device__ __forceinline__ ProjAngle proj_angle(int N, int B, double2 cs) {
-    const double c = cs.x, s = cs.y, hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
-    const double ac = fabs(c), as = fabs(s);
-    ProjAngle r;
+// host: projector constants of one angle (FP64, then fixed point / FP32)
+static ProjAngle make_proj_angle(int N, int B, double c, double s) {
+    const double hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
+    const double ac = std::fabs(c), as = std::fabs(s);
+    ProjAngle r{};
     double db, dm, k0, maj, mnr;
     if (ac >= as) {  // ray crosses each row once: column coordinate per row
         db = 1.0 / c;
@@ -145,10 +95,10 @@ __device__ __forceinline__ ProjAngle proj_angle(int N, int B, double2 cs) {
         mnr = ac;
         r.colmaj = 1;
     }
-    r.Db = __double2ll_rn(db * kFix);
-    r.Dm = __double2ll_rn(dm * kFix);
-    r.K0 = __double2ll_rn(k0 * kFix);
-    r.dm25 = (int)__double2ll_rn(dm * kFix25);
+    r.Db = std::llrint(db * kFix);
+    r.Dm = std::llrint(dm * kFix);
+    r.K0 = std::llrint(k0 * kFix);
+    r.dm25 = (int)std::llrint(dm * kFix25);
     const double kap = mnr > 0.0 ? maj / mnr : (double)kGammaCap;
     r.kappa = (float)kap;
     r.wf0 = (float)(0.5 + kap * 1.5);
@@ -157,41 +107,50 @@ __device__ __forceinline__ ProjAngle proj_angle(int N, int B, double2 cs) {
     return r;
 }
 
-struct BpAngle {
-    unsigned P0;       // bin coordinate of the tile's first pixel minus w0 (2^-25)
-    int C25, S25;      // cos, sin (2^-25): the steps of one pixel in x and y
-    int w0;            // first staged bin of this tile
-    float gam;         // weight slope in bin units, 1/min(|c|,|s|) (capped)
-    float wf0, wf1;    // weight constants (w_mid = max(|c|,|s|)/2)
-    float h;           // 1/max(|c|,|s|), folded into the staged sinogram values
-    const float* row;  // sinogram line
-};
-
-// tile origin (x0, y0), tile extent kBpTileX x kBpTileY
-__device__ __forceinline__ void bp_angle(BpAngle& r, int N, int B, double2 cs, int x0, int y0) {
-    const double c = cs.x, s = cs.y, hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
-    const double ac = fabs(c), as = fabs(s);
-    const double mx = fmax(ac, as), mn = fmin(ac, as);
-    // bin coordinate of pixel (i, j): j c - i s + (hB - hN c + hN s), in 2^-40
-    const long long C = __double2ll_rn(c * kFix), S = __double2ll_rn(s * kFix);
-    const long long K = __double2ll_rn((hB - hN * c + hN * s) * kFix);
-    long long lo = LLONG_MAX;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const long long j = x0 + ((k & 1) ? kBpTileX - 1 : 0);
-        const long long i = y0 + ((k & 2) ? kBpTileY - 1 : 0);
-        lo = min(lo, j * C - i * S + K);
-    }
-    r.w0 = (int)(lo >> 40) - 2;
-    const long long org = (long long)x0 * C - (long long)y0 * S + K;
-    r.P0 = (unsigned)((org - ((long long)r.w0 << 40)) >> 15);
-    r.C25 = (int)__double2ll_rn(c * kFix25);
-    r.S25 = (int)__double2ll_rn(s * kFix25);
+// host: backprojector constants of one angle
+static BpConst make_bp_const(int N, int B, double c, double s) {
+    const double hN = 0.5 * (N - 1), hB = 0.5 * (B - 1);
+    const double ac = std::fabs(c), as = std::fabs(s);
+    const double mx = std::fmax(ac, as), mn = std::fmin(ac, as);
+    BpConst r{};
+    r.C = std::llrint(c * kFix);
+    r.S = std::llrint(s * kFix);
+    r.K = std::llrint((hB - hN * c + hN * s) * kFix);
+    r.C25 = (int)std::llrint(c * kFix25);
+    r.S25 = (int)std::llrint(s * kFix25);
     const double gam = mn > 0.0 ? 1.0 / mn : (double)kGammaCap;
     r.gam = (float)gam;
     r.wf0 = (float)(0.5 + gam * (0.5 * mx + 1.0));
     r.wf1 = (float)(0.5 + gam * (0.5 * mx - 2.0));
     r.h = (float)(1.0 / mx);
+    return r;
+}
+
+// one angle of a backprojector chunk, for the chunk's tile
+struct __align__(16) BpAngle {
+    unsigned P0;    // bin coordinate of the tile's first pixel minus w0 (2^-25)
+    int C25, S25;   // steps of one pixel in x and y (2^-25)
+    int w0;         // first staged bin of this tile
+    float gam, wf0, wf1;
+    float h;           // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
+    const float* row;  // sinogram line
+};
+
+// tile origin (x0, y0), tile extent kBpTileX x kBpTileY: the lowest bin
+// coordinate over the tile is at the corner picked by the signs of C and S
+__device__ __forceinline__ void bp_tile_angle(BpAngle& r, const BpConst& k, int x0, int y0) {
+    const long long j = x0 + (k.C < 0 ? kBpTileX - 1 : 0);
+    const long long i = y0 + (k.S > 0 ? kBpTileY - 1 : 0);
+    const long long lo = j * k.C - i * k.S + k.K;
+    r.w0 = (int)(lo >> 40) - 2;
+    const long long org = (long long)x0 * k.C - (long long)y0 * k.S + k.K;
+    r.P0 = (unsigned)((org - ((long long)r.w0 << 40)) >> (40 - kFracBits));
+    r.C25 = k.C25;
+    r.S25 = k.S25;
+    r.gam = k.gam;
+    r.wf0 = k.wf0;
+    r.wf1 = k.wf1;
+    r.h = k.h;
 }
 
 // asynchronous 4-byte global -> shared copy; zero-fill when !valid
@@ -234,10 +193,21 @@ __device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map,
         : "memory");
 }
 
-// bounded wait for the given phase of a barrier; false when the bound ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the given phase of a barrier; false when the bound ran
+// out: `limit_ns` of global time (checked every 256 polls), or 2^28 polls
+// should the timer not advance
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase, uint64_t limit_ns = kWaitLimitNs) {
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-    for (int it = 0; it < (1 << 22); ++it) {
+    uint64_t t0 = 0;
+    for (unsigned it = 0; it < (1u << 28); ++it) {
         unsigned ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -245,8 +215,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned phase) {
             : "r"(b), "r"(phase)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 255u) {
+            const uint64_t t = global_ns();
+            if (it == 255u) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
     }
     return false;
+}
+
+// failure-detection self test: one thread waits on a barrier that nothing
+// arrives at, with the projector's bounded wait; when the bound runs out it
+// sets the timeout bit of the status word and returns (no copy is in flight)
+__global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit_ns)) atomicOr(status, 4);
 }
 
 // ------------------------------------------------------------------
@@ -279,10 +264,11 @@ __device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& b
 __device__ __forceinline__ int proj_bins(int na) { return na == 1 ? 128 : kProjThreads / na; }
 
 // NR consecutive rows of one ray inside a staged chunk: the two candidate
-// pixels of each row, weighted by the trapezoid (see the file header)
+// pixels of each row, weighted by the trapezoid (see the file header); the
+// two candidates accumulate in the two lanes of one packed FP32 pair
 template <int NR>
 __device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjAngle& A) {
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int pl = f0 + r * A.dm25;  // position - J at this row (2^-25), may be negative
@@ -290,10 +276,9 @@ __device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjA
         const float* t = base + r * kProjPitch + (pl >> kFracBits);  // lower candidate pixel
         const float w0 = __saturatef(fmaf(-A.kappa, F, A.wf0));
         const float w1 = __saturatef(fmaf(A.kappa, F, A.wf1));
-        acc = fmaf(w0, t[0], acc);
-        acc = fmaf(w1, t[1], acc);
+        acc = __ffma2_rn(make_float2(w0, w1), make_float2(t[0], t[1]), acc);
     }
-    return acc;
+    return acc.x + acc.y;
 }
 
 // staged minor range of chunk m0 of the item: extremes over its corner rays
@@ -347,7 +332,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
         }
         if (it >= p.n_items || s_bad) break;
         const ProjItem item = p.items[it];
-        if (tid < item.na) sa[tid] = proj_angle(N, B, c_trig[p.const_off + p.angs[item.ang0 + tid].angle]);
+        if (tid < item.na) sa[tid] = p.ptab[p.angs[item.ang0 + tid].angle];
         __syncthreads();
 
         const int na = item.na;
@@ -444,7 +429,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
             if (s_bad) continue;  // skip the compute; the loop top exits
             // this ray: integer part J and 2^-25 fraction of its position at its first row
             const int J = (int)(pos >> 40);
-            const int f0 = (int)((pos >> 15) & 0x1FFFFFF);
+            const int f0 = (int)((pos >> (40 - kFracBits)) & ((1 << kFracBits) - 1));
             const float* base = tile + r0 * kProjPitch + (J - q0);
             total += (na == 1) ? ray_rows<kProjRows / 2>(base, f0, A) : ray_rows<kProjRows>(base, f0, A);
         }
@@ -466,6 +451,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
             const size_t o = ((size_t)item.outb + ar.row) * B + b;
             float v = A.h * total;
             if (p.sub) v -= __ldg(p.sub + o);
+            if (p.prescale) v *= A.h;
             p.out[o] = v;
         }
         __syncthreads();  // sa / s_item / s_q0 reused by the next item
@@ -477,165 +463,211 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
 // ------------------------------------------------------------------
 enum { EPI_STORE = 0, EPI_USTEP = 1 };
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int NPENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING) : "memory");
+}
+
+// the angles of chunk a0.. of an item, for its tile (threads < chunk size)
+__device__ __forceinline__ void bp_chunk_setup(BpAngle* sa, const BpParams& p, const BpItem& item, int a0,
+                                               int tid) {
+    if (tid < min(kBpChunk, item.na - a0)) {
+        const AngRow ar = p.angs[item.ang0 + a0 + tid];
+        bp_tile_angle(sa[tid], p.btab[ar.angle], item.tx * kBpTileX, item.ty * kBpTileY);
+        sa[tid].row = p.sino + ((size_t)item.sinb + ar.row) * p.B;
+    }
+}
+
+// asynchronous copies of a chunk's windows, one commit group:
+// win[a][k] = (r[w0 + k], r[w0 + k + 1]) of the line, zero outside [0, B)
+__device__ __forceinline__ void bp_chunk_issue(float2* win, const BpAngle* sa, int nac, int B, int tid) {
+    for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
+        const int a = e / kBpWin, k = e - a * kBpWin;
+        const int b = sa[a].w0 + k;
+        const float* row = sa[a].row;
+        float* d = reinterpret_cast<float*>(win + e);
+        const bool v0 = (unsigned)b < (unsigned)B, v1 = (unsigned)(b + 1) < (unsigned)B;
+        cp_async4(d, v0 ? row + b : row, v0);
+        cp_async4(d + 1, v1 ? row + b + 1 : row, v1);
+    }
+    cp_async_commit();
+}
+
+// Persistent backprojector. A block walks a stream of chunks (an item's
+// angles, 32 at a time, then the next item's from the work queue): the
+// windows of the next chunk are copied asynchronously into the other stage
+// while the current one is accumulated, and an item's epilogue runs while
+// the next item's first windows are in flight.
 // 16 x 16 threads; thread (tx, ty) owns the 4 x 4 pixels (x0 + tx + 16 kx,
 // y0 + ty + 16 ky): a half-warp (16 consecutive tx) reads 16 window pairs
 // within 16 consecutive entries, so its 64-bit shared loads never conflict.
 template <int EPI>
 __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
-    __shared__ __align__(16) float2 win[kBpChunk][kBpWin];  // (h v[b], h v[b+1])
-    __shared__ BpAngle sa[kBpChunk];
+    extern __shared__ __align__(16) unsigned char bp_dyn[];
+    float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][kBpChunk][kBpWin]
+    __shared__ BpAngle sa[2][kBpChunk];
     __shared__ int s_item;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int N = p.N, B = p.B;
     const size_t n = (size_t)N * N;
 
-    for (int pass = 0;; ++pass) {
-        int it;
-        if (p.counter) {
-            if (tid == 0) s_item = atomicAdd(p.counter, 1);
-            __syncthreads();
-            it = s_item;
-        } else {
-            it = pass == 0 ? (int)blockIdx.x : p.n_items;
-        }
-        if (it >= p.n_items) break;
-        const BpItem item = p.items[it];
-        const int x0 = item.tx * kBpTileX, y0 = item.ty * kBpTileY;
-        float acc[4][4];
-#pragma unroll
-        for (int ky = 0; ky < 4; ++ky)
-#pragma unroll
-            for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
+    int pass = 0;
+    auto fetch = [&]() -> int {  // next work item (uniform over the block)
+        const int q = pass++;
+        if (!p.counter) return q == 0 ? (int)blockIdx.x : p.n_items;
+        if (tid == 0) s_item = atomicAdd(p.counter, 1);
+        __syncthreads();
+        return s_item;
+    };
 
-        for (int a0 = 0; a0 < item.na; a0 += kBpChunk) {
-            const int nac = min(kBpChunk, item.na - a0);
-            if (tid < nac) {
-                BpAngle& A = sa[tid];
-                const AngRow ar = p.angs[item.ang0 + a0 + tid];
-                bp_angle(A, N, B, c_trig[p.const_off + ar.angle], x0, y0);
-                A.row = p.sino + ((size_t)item.sinb + ar.row) * B;
-            }
+    int cur_it = fetch();
+    if (cur_it >= p.n_items) return;
+    BpItem cur = p.items[cur_it];
+    int a0 = 0, buf = 0;
+    bp_chunk_setup(sa[0], p, cur, 0, tid);
+    __syncthreads();
+    bp_chunk_issue(wins, sa[0], min(kBpChunk, cur.na), B, tid);
+
+    float acc[4][4];
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
+
+    for (;;) {
+        // the chunk after this one: the rest of this item, else the next item's first
+        int nxt_it = cur_it, na0 = a0 + kBpChunk;
+        if (na0 >= cur.na) {
+            nxt_it = fetch();
+            na0 = 0;
+        }
+        const bool more = nxt_it < p.n_items;
+        BpItem nxt = cur;
+        if (more) {
+            if (nxt_it != cur_it) nxt = p.items[nxt_it];
+            bp_chunk_setup(sa[buf ^ 1], p, nxt, na0, tid);
             __syncthreads();
-            if (nac == kBpChunk) {  // full chunk: fixed trip count, loads in flight together
-                constexpr int kPer = kBpChunk * kBpWin / kBpThreads, kHalf = kPer / 2;
+            bp_chunk_issue(wins + (buf ^ 1) * kBpStageFloat2, sa[buf ^ 1], min(kBpChunk, nxt.na - na0), B, tid);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        if (!p.prescaled) {  // fold h into the pairs this thread copied (its own copies have landed)
+            float2* w = wins + buf * kBpStageFloat2;
+            const int nac = min(kBpChunk, cur.na - a0);
+            for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
+                const float h = sa[buf][e / kBpWin].h;
+                const float2 v = w[e];
+                w[e] = make_float2(h * v.x, h * v.y);
+            }
+        }
+        __syncthreads();  // every thread's copies of this chunk have landed
+
+        const float2* win = wins + buf * kBpStageFloat2;
+        const BpAngle* sab = sa[buf];
+        const int nac = min(kBpChunk, cur.na - a0);
+        for (int a = 0; a < nac; ++a) {
+            const BpAngle& A = sab[a];
+            const float2* wa = win + a * kBpWin;
+            const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
+            // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
+            const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
+            const unsigned cx = (unsigned)A.C25 << 4, sy = (unsigned)A.S25 << 4;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    float v0[kHalf], v1[kHalf];
+            for (int ky = 0; ky < 4; ++ky) {
+                const unsigned prow = pb - (unsigned)ky * sy;
 #pragma unroll
-                    for (int i = 0; i < kHalf; ++i) {
-                        const int e = tid + (half * kHalf + i) * kBpThreads;
-                        const int a = e / kBpWin, k = e - a * kBpWin;
-                        const int b = sa[a].w0 + k;
-                        const float* row = sa[a].row;
-                        v0[i] = ((unsigned)b < (unsigned)B) ? __ldg(row + b) : 0.f;
-                        v1[i] = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(row + b + 1) : 0.f;
-                    }
+                for (int kx = 0; kx < 4; ++kx) {
+                    const unsigned pp = prow + (unsigned)kx * cx;
+                    const float F = one_plus_frac25((int)pp);
+                    const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
+                    const float w0 = __saturatef(fmaf(-gam, F, wf0));
+                    const float w1 = __saturatef(fmaf(gam, F, wf1));
+                    acc[ky][kx] = fmaf(w0, r.x, acc[ky][kx]);
+                    acc[ky][kx] = fmaf(w1, r.y, acc[ky][kx]);
+                }
+            }
+        }
+
+        if (a0 + kBpChunk >= cur.na) {  // the item's last chunk: epilogue
+
+            const int x0 = cur.tx * kBpTileX, y0 = cur.ty * kBpTileY;
+            if (EPI == EPI_STORE) {
+                float* img = p.img + (size_t)cur.img * n;
 #pragma unroll
-                    for (int i = 0; i < kHalf; ++i) {
-                        const int e = tid + (half * kHalf + i) * kBpThreads;
-                        const int a = e / kBpWin, k = e - a * kBpWin;
-                        const float h = sa[a].h;
-                        win[a][k] = make_float2(h * v0[i], h * v1[i]);
+                for (int ky = 0; ky < 4; ++ky) {
+                    const int row = y0 + ty + 16 * ky;
+                    if (row >= N) continue;
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx) {
+                        const int col = x0 + tx + 16 * kx;
+                        if (col >= N) continue;
+                        float* o = img + (size_t)row * N + col;
+                        *o = (p.beta != 0.f ? *o : 0.f) + acc[ky][kx];
                     }
                 }
             } else {
-                for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
-                    const int a = e / kBpWin, k = e - a * kBpWin;
-                    const BpAngle& A = sa[a];
-                    const int b = A.w0 + k;
-                    const float v0 = ((unsigned)b < (unsigned)B) ? __ldg(A.row + b) : 0.f;
-                    const float v1 = ((unsigned)(b + 1) < (unsigned)B) ? __ldg(A.row + b + 1) : 0.f;
-                    win[a][k] = make_float2(A.h * v0, A.h * v1);
-                }
-            }
-            __syncthreads();
-            for (int a = 0; a < nac; ++a) {
-                const BpAngle& A = sa[a];
-                const float2* wa = win[a];
-                const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
-                // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
-                const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
-                const unsigned cx = (unsigned)A.C25 << 4, sy = (unsigned)A.S25 << 4;
+                // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
+                const BpView& V = p.view;
+                const int k = *V.iter;
+                const float eta = V.eta1[cur.node];
+                float* u = V.u + (size_t)cur.img * n;
+                const float* lam = V.lam + (size_t)cur.img * n;
 #pragma unroll
                 for (int ky = 0; ky < 4; ++ky) {
-                    const unsigned prow = pb - (unsigned)ky * sy;
+                    const int row = y0 + ty + 16 * ky;
+                    if (row >= N) continue;
+                    const int seg = V.seg_of_row[row];
+                    const int mi = cur.node * V.M + seg;
+                    const int j = k - V.lag[mi];
+                    const float* xv = nullptr;
+                    if (j >= 1)
+                        xv = V.hist + ((((size_t)(j % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +
+                             (size_t)row * N;
 #pragma unroll
                     for (int kx = 0; kx < 4; ++kx) {
-                        const unsigned pp = prow + (unsigned)kx * cx;
-                        const float F = one_plus_frac25((int)pp);
-                        const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
-                        const float w0 = __saturatef(fmaf(-gam, F, wf0));
-                        const float w1 = __saturatef(fmaf(gam, F, wf1));
-                        acc[ky][kx] = fmaf(w0, r.x, acc[ky][kx]);
-                        acc[ky][kx] = fmaf(w1, r.y, acc[ky][kx]);
+                        const int col = x0 + tx + 16 * kx;
+                        if (col >= N) continue;
+                        const size_t o = (size_t)row * N + col;
+                        const float uo = u[o];
+                        const float x = xv ? xv[col] : 0.f;
+                        const float g = acc[ky][kx] + V.rho * (uo - x) + lam[o];
+                        acc[ky][kx] = uo - eta * g;
+                        u[o] = acc[ky][kx];
+                    }
+                }
+                if (V.uT) {  // the transposed copy read by the projector's steep-ray items
+                    // 64 x 65 floats in this chunk's stage, free once every thread is done with it
+                    float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
+                    __syncthreads();
+#pragma unroll
+                    for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+                        for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 16 * ky] = acc[ky][kx];
+                    __syncthreads();
+                    float* ut = V.uT + (size_t)cur.img * n;
+#pragma unroll
+                    for (int i = 0; i < kBpTileX * kBpTileY / kBpThreads; ++i) {
+                        const int e = tid + i * kBpThreads;
+                        const int cc = e >> 6, rr = e & 63;
+                        if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
                     }
                 }
             }
-            __syncthreads();
+#pragma unroll
+            for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
         }
-
-        if (EPI == EPI_STORE) {
-            float* img = p.img + (size_t)item.img * n;
-#pragma unroll
-            for (int ky = 0; ky < 4; ++ky) {
-                const int row = y0 + ty + 16 * ky;
-                if (row >= N) continue;
-#pragma unroll
-                for (int kx = 0; kx < 4; ++kx) {
-                    const int col = x0 + tx + 16 * kx;
-                    if (col >= N) continue;
-                    float* o = img + (size_t)row * N + col;
-                    *o = (p.beta != 0.f ? *o : 0.f) + acc[ky][kx];
-                }
-            }
-        } else {
-            // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
-            const BpView& V = p.view;
-            const int k = *V.iter;
-            const float eta = V.eta1[item.node];
-            float* u = V.u + (size_t)item.img * n;
-            const float* lam = V.lam + (size_t)item.img * n;
-#pragma unroll
-            for (int ky = 0; ky < 4; ++ky) {
-                const int row = y0 + ty + 16 * ky;
-                if (row >= N) continue;
-                const int seg = V.seg_of_row[row];
-                const int mi = item.node * V.M + seg;
-                const int j = k - V.lag[mi];
-                const float* xv = nullptr;
-                if (j >= 1)
-                    xv = V.hist + ((((size_t)(j % V.D) * 3 + V.kind[mi]) * V.S + item.slice) * n) +
-                         (size_t)row * N;
-#pragma unroll
-                for (int kx = 0; kx < 4; ++kx) {
-                    const int col = x0 + tx + 16 * kx;
-                    if (col >= N) continue;
-                    const size_t o = (size_t)row * N + col;
-                    const float uo = u[o];
-                    const float x = xv ? xv[col] : 0.f;
-                    const float g = acc[ky][kx] + V.rho * (uo - x) + lam[o];
-                    acc[ky][kx] = uo - eta * g;
-                    u[o] = acc[ky][kx];
-                }
-            }
-            if (V.uT) {  // the transposed copy read by the projector's steep-ray items
-                float* T = reinterpret_cast<float*>(win);  // 64 x 65 floats, free after the angle loop
-#pragma unroll
-                for (int ky = 0; ky < 4; ++ky)
-#pragma unroll
-                    for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 16 * ky] = acc[ky][kx];
-                __syncthreads();
-                float* ut = V.uT + (size_t)item.img * n;
-#pragma unroll
-                for (int i = 0; i < kBpTileX * kBpTileY / kBpThreads; ++i) {
-                    const int e = tid + i * kBpThreads;
-                    const int cc = e >> 6, rr = e & 63;
-                    if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
-                }
-                __syncthreads();  // the window buffer is reused by the next item
-            }
-        }
+        __syncthreads();  // this stage and sa[buf] are refilled two chunks on
+        if (!more) break;
+        cur = nxt;
+        cur_it = nxt_it;
+        a0 = na0;
+        buf ^= 1;
     }
 }
 
@@ -716,15 +748,37 @@ void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
     TOMO_CUDA(cudaGetLastError());
 }
 
+// the window stages (48 KB) and the largest shared carveout, so that four
+// blocks of each epilogue form fit on an SM; set once per process
+static void ensure_bp_attr() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(backproject_kernel<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBpSmem);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(backproject_kernel<EPI_USTEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kBpSmem);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(backproject_kernel<EPI_STORE>,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(backproject_kernel<EPI_USTEP>,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    });
+    TOMO_CUDA(err);
+}
+
 void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st) {
     if (p.n_items == 0) return;
-    backproject_kernel<EPI_STORE><<<grid, kBpThreads, 0, st>>>(p);
+    ensure_bp_attr();
+    backproject_kernel<EPI_STORE><<<grid, kBpThreads, kBpSmem, st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
 void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st) {
     if (p.n_items == 0) return;
-    backproject_kernel<EPI_USTEP><<<grid, kBpThreads, 0, st>>>(p);
+    ensure_bp_attr();
+    backproject_kernel<EPI_USTEP><<<grid, kBpThreads, kBpSmem, st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
@@ -745,12 +799,13 @@ int persistent_grid_project() {
 
 int persistent_grid_backproject(bool ustep) {
     int per_sm = 0;
+    ensure_bp_attr();
     if (ustep)
         TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_USTEP>,
-                                                                kBpThreads, 0));
+                                                                kBpThreads, kBpSmem));
     else
         TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_STORE>,
-                                                                kBpThreads, 0));
+                                                                kBpThreads, kBpSmem));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -975,7 +1030,8 @@ tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* 
         g->c.resize(n_angles);
         g->s.resize(n_angles);
         const double half_pi = 1.57079632679489661923;
-        std::vector<double2> cs(n_angles);
+        std::vector<ProjAngle> pt(n_angles);
+        std::vector<BpConst> bt(n_angles);
         for (int a = 0; a < n_angles; ++a) {
             const double th = angles_rad ? angles_rad[a] : a * (3.14159265358979323846 / n_angles);
             if (!std::isfinite(th)) {
@@ -994,26 +1050,24 @@ tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* 
             }
             g->c[a] = c;
             g->s[a] = s;
-            cs[a] = make_double2(c, s);
+            pt[a] = make_proj_angle(N, n_bins, c, s);
+            bt[a] = make_bp_const(N, n_bins, c, s);
         }
         cudaError_t e = cudaGetDevice(&g->device);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_ptab, sizeof(ProjAngle) * n_angles);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_btab, sizeof(BpConst) * n_angles);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int) * 4);
+        if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int) * 4);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_ptab, pt.data(), sizeof(ProjAngle) * n_angles, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_btab, bt.data(), sizeof(BpConst) * n_angles, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
+            cudaFree(g->d_ptab);
+            cudaFree(g->d_btab);
+            cudaFree(g->d_status);
             delete g;
-            fail(TOMO_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-        }
-        g->const_off = pool_alloc(g->device, n_angles);
-        if (g->const_off < 0) {
-            delete g;
-            fail(TOMO_ERR_WORKSPACE, "constant trig pool exhausted (" +
-                                         std::to_string(TOMO_MAX_CONST_ANGLES) +
-                                         " angles shared by all live geometries)");
-        }
-        e = cudaMemcpyToSymbol(c_trig, cs.data(), sizeof(double2) * n_angles,
-                               sizeof(double2) * g->const_off, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            pool_free(g->device, g->const_off, n_angles);
-            delete g;
-            fail(TOMO_ERR_CUDA, std::string("cudaMemcpyToSymbol: ") + cudaGetErrorString(e));
+            fail(TOMO_ERR_CUDA, std::string("tomo_geometry_create: ") + cudaGetErrorString(e));
         }
         *out = reinterpret_cast<tomo_geometry_t>(g);
     });
@@ -1028,7 +1082,9 @@ tomo_status tomo_geometry_destroy(tomo_geometry_t gh) {
             cudaFree(s.d_pitems);
             cudaFree(s.d_bitems);
         }
-        pool_free(g->device, g->const_off, g->A);
+        cudaFree(g->d_ptab);
+        cudaFree(g->d_btab);
+        cudaFree(g->d_status);
         delete g;
     });
 }
@@ -1095,11 +1151,12 @@ tomo_status tomo_project(tomo_geometry_t gh, const float* img, float* sino, cons
         p.items = s.d_pitems;
         p.angs = s.d_angs;
         p.counter = nullptr;
-        p.status = nullptr;
+        p.status = g->d_status;
         p.n_items = s.n_pitems;
+        p.ptab = g->d_ptab;
         p.N = g->N;
         p.B = g->B;
-        p.const_off = g->const_off;
+        p.prescale = 0;
         launch_project(p, s.n_pitems, (cudaStream_t)stream);
     });
 }
@@ -1121,9 +1178,10 @@ tomo_status tomo_backproject(tomo_geometry_t gh, const float* sino, float* img, 
         p.items = s.d_bitems;
         p.angs = s.d_angs;
         p.n_items = s.n_bitems;
+        p.btab = g->d_btab;
         p.N = g->N;
         p.B = g->B;
-        p.const_off = g->const_off;
+        p.prescaled = 0;
         p.beta = beta;
         launch_backproject_store(p, s.n_bitems, (cudaStream_t)stream);
     });
@@ -1170,6 +1228,32 @@ tomo_status tomo_opnorm_sq(tomo_geometry_t gh, const int32_t* angle_idx, int n_s
         TOMO_CUDA(cudaMemcpyAsync(h, dots, sizeof(h), cudaMemcpyDeviceToHost, st));
         TOMO_CUDA(cudaStreamSynchronize(st));
         *out = h[0];  // Rayleigh quotient at the unit vector x
+        const tomo_status rc = tomo_sync_status(gh, stream);
+        if (rc != TOMO_OK) fail(rc, tomo_last_error());
+    });
+}
+
+tomo_status tomo_selftest_wait(tomo_geometry_t gh, int timeout_ms, tomo_stream_t stream) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        TOMO_REQUIRE(timeout_ms >= 1 && timeout_ms <= 2000, "timeout_ms must be in [1, 2000]");
+        wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(g->d_status, (uint64_t)timeout_ms * 1000000ull);
+        TOMO_CUDA(cudaGetLastError());
+    });
+}
+
+tomo_status tomo_sync_status(tomo_geometry_t gh, tomo_stream_t stream) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        cudaStream_t st = (cudaStream_t)stream;
+        int status = 0;
+        TOMO_CUDA(cudaMemcpyAsync(&status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TOMO_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(int), st));
+        TOMO_CUDA(cudaStreamSynchronize(st));
+        if (status & 4) fail(TOMO_ERR_TIMEOUT, "a bounded wait for a staged image band gave up; the projection is incomplete");
+        if (status & 1) fail(TOMO_ERR_CUDA, "projector staging extent exceeded (internal error)");
     });
 }
 

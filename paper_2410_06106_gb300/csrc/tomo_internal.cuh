@@ -108,12 +108,45 @@ constexpr int kBpTileX = 64, kBpTileY = 64;
 constexpr int kBpChunk = 32;  // angles staged per pass
 constexpr int kBpWin = 96;    // window pairs per angle: 63 (|c| + |s|) + 6 < 96
 
+constexpr int kBpStageFloat2 = kBpChunk * kBpWin;  // one window stage; two stages in flight
+constexpr int kBpSmem = 2 * kBpStageFloat2 * (int)sizeof(float2);
+
 constexpr double kFix = 1099511627776.0;  // 2^40, fixed-point scale of positions
+
+// ------------------------------------------------------------------
+// per-angle operator constants, derived on the host in FP64 when a
+// geometry is created and kept in a device table per geometry
+// ------------------------------------------------------------------
+
+// projector: ray b at major index m has minor coordinate b Db + m Dm + K0
+// (2^-40); the trapezoid weights of its two candidate pixels are
+// sat(wf0 - kappa F) and sat(wf1 + kappa F) (F = 1 + fraction), times h
+struct ProjAngle {
+    long long Db, Dm, K0;
+    int dm25;      // Dm in 2^-25, for stepping inside a chunk
+    float kappa;   // |major| / |minor|: the weight slope in minor-index units
+    float wf0, wf1;
+    float h;       // 1 / |major|
+    int colmaj;    // 0: image rows are the major axis; 1: columns
+};
+
+// backprojector: pixel (i, j) sits at bin coordinate j C - i S + K (2^-40);
+// weights of its two candidate bins sat(wf0 - gam F), sat(wf1 + gam F)
+struct BpConst {
+    long long C, S, K;
+    int C25, S25;    // cos, sin in 2^-25: the steps of one pixel in x and y
+    float gam;       // 1 / min(|c|, |s|) (capped at 2^20)
+    float wf0, wf1;
+    float h;         // 1 / max(|c|, |s|)
+    int pad[2];
+};
 
 struct Geometry {
     int N = 0, B = 0, A = 0;
     int device = -1;
-    int const_off = -1;  // first slot of this geometry in the constant trig pool
+    ProjAngle* d_ptab = nullptr;  // [A] projector constants
+    BpConst* d_btab = nullptr;    // [A] backprojector constants
+    int* d_status = nullptr;  // device status word of standalone operator calls (bit 4: a wait gave up)
     std::vector<double> c, s;
     // cached device work lists of standalone project/backproject calls
     struct Sel {
@@ -151,11 +184,13 @@ struct ProjParams {
     const float* sub;  // may be null
     const ProjItem* items;
     const AngRow* angs;
+    const ProjAngle* ptab;
     int* counter;  // null: one block per item; else persistent work queue
     int* status;   // device error word (may be null)
     int n_items;
-    int N, B, const_off;
+    int N, B;
     int has_map, has_mapT;
+    int prescale;  // 1: write h (h P u - sub), the input the backprojector stages
 };
 
 // TMA descriptor of nimg images [N][N] float32 at base with a 32 x 256 box;
@@ -177,14 +212,16 @@ struct BpView {  // dADMM epilogue: where every node's view of x lives
 };
 
 struct BpParams {
-    const float* sino;
-    float* img;  // EPI_STORE target
+    const float* sino;  // lines r_a, or h_a r_a when prescaled (the projector's prescaled output)
+    float* img;         // EPI_STORE target
     const BpItem* items;
     const AngRow* angs;
+    const BpConst* btab;
     int* counter;
     int* status;
     int n_items;
-    int N, B, const_off;
+    int N, B;
+    int prescaled;  // 1: sino lines already carry the factor h_a
     float beta;
     BpView view;
 };

@@ -33,13 +33,20 @@ def test_project_function_adjoint_on_64_directions_full_size():
     y = autograd.project(u, g)
     (y * w).sum().backward()
     grad = u.grad.detach()
-    errs = []
+    wd = w.double()
+    wn = torch.linalg.norm(wd).item()
+    fd_err, dot_err = [], []
     for k in range(64):
         v = cuda(np.random.default_rng(100 + k).standard_normal((N, N)))
-        fd = (torch.sum(g.project(u0 + v).double() * w.double()) - torch.sum(g.project(u0 - v).double() * w.double())) / 2
-        ad = torch.sum(grad.double() * v.double())
-        errs.append(abs(fd.item() - ad.item()) / abs(ad.item()))
-    assert max(errs) <= 1e-4, max(errs)
+        yp, ym, pv = (g.project(t).double() for t in (u0 + v, u0 - v, v))
+        fd = (torch.sum(yp * wd) - torch.sum(ym * wd)).item() / 2
+        ad = torch.sum(grad.double() * v.double()).item()
+        # errors on the scale of the FP32 values that were formed: |w| |P(u0 +- v)| for the
+        # central difference, |w| |P v| for the dot test <w, P v> = <P^T w, v>
+        fd_err.append(abs(fd - ad) / (wn * max(torch.linalg.norm(yp).item(), torch.linalg.norm(ym).item())))
+        dot_err.append(abs(torch.sum(pv * wd).item() - ad) / (wn * torch.linalg.norm(pv).item()))
+    assert max(fd_err) <= 1e-5, max(fd_err)
+    assert max(dot_err) <= 1e-5, max(dot_err)
     og = O.Geometry(N, B, theta)
     pix = rng.integers(0, N * N, 64)
     ref = og.backproject_pixels(w.cpu().numpy(), pix)
@@ -91,8 +98,12 @@ def test_unrolled_admm_gradients_match_oracle_finite_differences():
 
 def test_unrolled_admm_full_size_checkpointed():
     """1024^2, 1440 angles, 8 nodes (interleaved, complete graph), 10 unrolled
-    iterations with per-iteration checkpoints: gradients against central
-    differences of the GPU forward"""
+    iterations. Checkpointing (one per iteration) changes no gradient and
+    keeps the peak memory well below the stored-activation run; the sinogram
+    gradient matches central differences of the GPU forward (the map is
+    linear in d, so they are exact up to FP32 rounding); the rho gradient
+    matches them to the FP32 forward's noise (the 1e-3 check of the rho
+    gradient against the FP64 oracle runs on the small problem above)"""
     need_gpu()
     prob = synth.make_problem("c4_diff")
     gd = prob["geometry"]
@@ -105,22 +116,33 @@ def test_unrolled_admm_full_size_checkpointed():
     w = cuda(rng.standard_normal((gd["N"], gd["N"])))
     sino = cuda(prob["sino"][0])
 
-    def loss_of(rho_val, d, grad=False):
+    def loss_of(rho_val, d, grad=False, checkpoint=True):
         rho = torch.tensor(rho_val, dtype=torch.float64, requires_grad=grad)
-        x = autograd.unrolled_admm(d, g, sel, prob["seg_row_ptr"], rho, eta, iters=10, checkpoint=True)
+        x = autograd.unrolled_admm(d, g, sel, prob["seg_row_ptr"], rho, eta, iters=10, checkpoint=checkpoint)
         return torch.sum(x.double() * w.double()), rho
 
-    torch.cuda.reset_peak_memory_stats()
-    d = sino.clone().requires_grad_(True)
-    loss, rho = loss_of(1.0, d, grad=True)
-    loss.backward()
-    h = 1e-2
-    with torch.no_grad():
-        fd = (loss_of(1.0 + h, sino)[0] - loss_of(1.0 - h, sino)[0]).item() / (2 * h)
-    assert abs(rho.grad.item() - fd) <= 1e-3 * abs(fd), (rho.grad.item(), fd)
+    grads, peaks = [], []
+    for ck in (True, False):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        d = sino.clone().requires_grad_(True)
+        loss, rho = loss_of(1.0, d, grad=True, checkpoint=ck)
+        loss.backward()
+        torch.cuda.synchronize()
+        peaks.append(torch.cuda.max_memory_allocated() - base)
+        grads.append((rho.grad.item(), d.grad.detach().clone()))
+        del loss, rho, d
+    assert grads[0][0] == grads[1][0] and torch.equal(grads[0][1], grads[1][1])
+    assert peaks[0] < 0.25 * peaks[1], peaks
+    g_rho, g_d = grads[0]
     v = torch.randn(sino.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     with torch.no_grad():
         fdd = (loss_of(1.0, sino + v)[0] - loss_of(1.0, sino - v)[0]).item() / 2
-    add = float(torch.sum(d.grad.double() * v.double()))
+    add = float(torch.sum(g_d.double() * v.double()))
     assert abs(add - fdd) <= 1e-3 * abs(fdd), (add, fdd)
+    h = 0.05
+    with torch.no_grad():
+        fd = (loss_of(1.0 + h, sino)[0] - loss_of(1.0 - h, sino)[0]).item() / (2 * h)
+    assert abs(g_rho - fd) <= 2e-2 * abs(fd), (g_rho, fd)
     g.close()

@@ -66,3 +66,41 @@ def test_undersized_workspace_and_nonfinite_data():
         s.step(sino, 1)
     assert e.value.code == NUMERIC
     assert s.k == 1
+
+
+TIMEOUT = -4
+
+
+def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
+    """the projector's bounded wait, run on a barrier that nothing completes
+    (no copy in flight), gives up, the status word reports TOMO_ERR_TIMEOUT on
+    the host, and the same context keeps computing correct projections"""
+    need_gpu()
+    lib = api.lib()
+    g = api.Geometry(64, 91, A=90)
+    x = torch.rand(64, 64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    ref = g.project(x)
+    g.sync_status()  # clean
+    assert lib.tomo_selftest_wait(g.handle, 20, C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    with pytest.raises(api.TomoError) as e:
+        g.sync_status()
+    assert e.value.code == TIMEOUT and b"bounded wait" in lib.tomo_last_error()
+    g.sync_status()  # the read reset the word
+    assert torch.equal(g.project(x), ref)
+    g.sync_status()
+    assert lib.tomo_selftest_wait(g.handle, 0, None) == INVALID
+    g.close()
+
+
+def test_dadmm_status_without_stats():
+    need_gpu()
+    p = small_problem(N=16, A=16, B=23, M=2, graph="ring", quant="none")
+    s = api.DADMM(p, np.full(2, 0.002))
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s.step(sino, 2, stats=False)
+    s.sync_status()
+    sino[0, 3, 5] = float("nan")
+    s.step(sino, 1, stats=False)
+    with pytest.raises(api.TomoError) as e:
+        s.sync_status()
+    assert e.value.code == NUMERIC
