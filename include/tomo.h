@@ -305,7 +305,9 @@ TOMO_API tomo_status dadmm_step(dadmm_t h, const dadmm_state* st, const float* s
  * read (dadmm_step with stats reads and resets it itself): reads and resets
  * the word on `stream`, synchronizes, and returns TOMO_ERR_TIMEOUT (a bounded
  * device wait gave up; the iterate is incomplete), TOMO_ERR_NUMERIC
- * (non-finite statistics), TOMO_ERR_CUDA (internal error) or TOMO_OK. */
+ * (non-finite statistics), TOMO_ERR_CUDA (internal error) or TOMO_OK. The
+ * word lives in the workspace; the first call of this handle on a workspace
+ * (step or status read) zeroes it, so fresh memory needs no initialisation. */
 TOMO_API tomo_status dadmm_sync_status(dadmm_t h, void* workspace, size_t workspace_bytes,
                                        tomo_stream_t stream);
 

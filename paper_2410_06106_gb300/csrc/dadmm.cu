@@ -52,6 +52,7 @@ struct Dadmm {
     AngRow* d_angs = nullptr;
     ProjItem* d_pitems = nullptr;   // batched order (longest first)
     BpItem* d_bitems = nullptr;
+    BpConst* d_bk = nullptr;  // backprojector constants of the node-major angle list
     ProjItem* d_pplain = nullptr;   // grouped by (slice, node)
     BpItem* d_bplain = nullptr;
     int n_pitems = 0, n_bitems = 0;
@@ -73,6 +74,7 @@ struct Dadmm {
     // workspace layout (byte offsets from the aligned base)
     size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_dual = 0,
            off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
+    const void* ws_status_init = nullptr;  // workspace whose status word this handle has zeroed
     // TMA descriptors of u and of its transposed copy (rebuilt with the graph)
     CUtensorMap map_u{}, map_uT{};
     int has_maps = 0;
@@ -435,7 +437,7 @@ static void free_dadmm(Dadmm* h) {
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->own) cudaStreamDestroy(h->own);
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
-    void* ptrs[] = {h->d_angs, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
+    void* ptrs[] = {h->d_angs, h->d_bk, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
                     h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_mx, h->d_km, h->d_jp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -533,8 +535,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     pp.prescale = 1;  // the residual is stored as h_a r_a, the form the backprojector stages
     BpParams bp{};
     bp.sino = w.resid;
-    bp.angs = h.d_angs;
-    bp.btab = h.g->d_btab;
+    bp.bk = h.d_bk;
     bp.status = w.status;
     bp.N = h.N;
     bp.B = h.B;
@@ -842,6 +843,7 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             std::vector<ProjItem> pb = pplain;
             std::vector<BpItem> bb = bplain;
             h->d_angs = device_upload(angs);
+            h->d_bk = device_upload(bp_list_consts(*g, angs));
             h->d_pitems = device_upload(pb);
             h->d_bitems = device_upload(bb);
             h->d_pplain = device_upload(pplain);
@@ -962,6 +964,11 @@ tomo_status dadmm_sync_status(dadmm_t hh, void* workspace, size_t workspace_byte
                      "workspace too small: need " + std::to_string(h.ws_bytes) + " bytes");
         const WsPtrs w = ws_ptrs(h, workspace);
         cudaStream_t st = (cudaStream_t)stream;
+        if (workspace != h.ws_status_init) {  // no iteration has run on this workspace yet
+            TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+            h.ws_status_init = workspace;
+            return;
+        }
         int status = 0;
         TOMO_CUDA(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
         TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
@@ -995,7 +1002,10 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
         if (stats) {
             TOMO_CUDA(cudaMemcpyAsync(&k0, st->iter, sizeof(int), cudaMemcpyDeviceToHost, user));
             TOMO_CUDA(cudaStreamSynchronize(user));
+        }
+        if (stats || workspace != h.ws_status_init) {  // the status word covers this call (or starts here)
             TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), user));
+            h.ws_status_init = workspace;
         }
         // TMA descriptors of u and u^T; u^T is refreshed from u at every call (the state may
         // have been set from outside), then kept in step by the u-step epilogue

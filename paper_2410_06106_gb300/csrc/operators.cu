@@ -132,8 +132,7 @@ struct __align__(16) BpAngle {
     int C25, S25;   // steps of one pixel in x and y (2^-25)
     int w0;         // first staged bin of this tile
     float gam, wf0, wf1;
-    float h;           // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
-    const float* row;  // sinogram line
+    float h;        // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
 };
 
 // tile origin (x0, y0), tile extent kBpTileX x kBpTileY: the lowest bin
@@ -470,36 +469,33 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING) : "memory");
 }
 
-// the angles of chunk a0.. of an item, for its tile (threads < chunk size)
-__device__ __forceinline__ void bp_chunk_setup(BpAngle* sa, const BpParams& p, const BpItem& item, int a0,
-                                               int tid) {
-    if (tid < min(kBpChunk, item.na - a0)) {
-        const AngRow ar = p.angs[item.ang0 + a0 + tid];
-        bp_tile_angle(sa[tid], p.btab[ar.angle], item.tx * kBpTileX, item.ty * kBpTileY);
-        sa[tid].row = p.sino + ((size_t)item.sinb + ar.row) * p.B;
+// asynchronous copies of a chunk's windows: win[a][k] = (r[w0 + k], r[w0 + k + 1])
+// of the line, zero outside [0, B); warp w takes angles w, w + 8, ...
+__device__ __forceinline__ void bp_issue_windows(float2* win, const BpAngle* sa, const float* const* rows, int nac,
+                                                 int B, int tid) {
+    static_assert(kBpWin == 96, "three pairs per lane");
+    const int lane = tid & 31;
+    for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
+        const int w0 = sa[a].w0;
+        const float* row = rows[a];
+        float* d = reinterpret_cast<float*>(win + a * kBpWin);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int k = lane + 32 * q, b = w0 + k;
+            const bool v0 = (unsigned)b < (unsigned)B, v1 = (unsigned)(b + 1) < (unsigned)B;
+            cp_async4(d + 2 * k, v0 ? row + b : row, v0);
+            cp_async4(d + 2 * k + 1, v1 ? row + b + 1 : row, v1);
+        }
     }
 }
 
-// asynchronous copies of a chunk's windows, one commit group:
-// win[a][k] = (r[w0 + k], r[w0 + k + 1]) of the line, zero outside [0, B)
-__device__ __forceinline__ void bp_chunk_issue(float2* win, const BpAngle* sa, int nac, int B, int tid) {
-    for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
-        const int a = e / kBpWin, k = e - a * kBpWin;
-        const int b = sa[a].w0 + k;
-        const float* row = sa[a].row;
-        float* d = reinterpret_cast<float*>(win + e);
-        const bool v0 = (unsigned)b < (unsigned)B, v1 = (unsigned)(b + 1) < (unsigned)B;
-        cp_async4(d, v0 ? row + b : row, v0);
-        cp_async4(d + 1, v1 ? row + b + 1 : row, v1);
-    }
-    cp_async_commit();
-}
-
-// Persistent backprojector. A block walks a stream of chunks (an item's
-// angles, 32 at a time, then the next item's from the work queue): the
-// windows of the next chunk are copied asynchronously into the other stage
-// while the current one is accumulated, and an item's epilogue runs while
-// the next item's first windows are in flight.
+// Persistent backprojector. A block takes work items from the queue and walks
+// their angles in chunks of 32. Everything a chunk needs arrives by cp.async
+// ahead of use, so no global latency sits between two chunks: while chunk i
+// accumulates, the windows of chunk i + 1, the per-angle constants of chunk
+// i + 2 and the descriptor of the item three items ahead are in flight, and
+// the queue has already been asked for the item after that. An item's
+// epilogue (Algorithm 2 step or store) overlaps the next chunk's copies.
 // 16 x 16 threads; thread (tx, ty) owns the 4 x 4 pixels (x0 + tx + 16 kx,
 // y0 + ty + 16 ky): a half-warp (16 consecutive tx) reads 16 window pairs
 // within 16 consecutive entries, so its 64-bit shared loads never conflict.
@@ -507,29 +503,71 @@ template <int EPI>
 __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
     extern __shared__ __align__(16) unsigned char bp_dyn[];
     float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][kBpChunk][kBpWin]
-    __shared__ BpAngle sa[2][kBpChunk];
-    __shared__ int s_item;
+    __shared__ BpConst s_k[kBpChunk];                  // constants of the chunk after next
+    __shared__ BpAngle s_a[2][kBpChunk];               // this chunk and the next, for their tiles
+    __shared__ const float* s_row[2][kBpChunk];
+    __shared__ BpItem s_d[4];                          // descriptors of the block's items j .. j + 3
+    __shared__ int s_idx[4];                           // their queue indices (>= n_items: none)
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int N = p.N, B = p.B;
     const size_t n = (size_t)N * N;
+    const int n_items = p.n_items;
 
-    int pass = 0;
-    auto fetch = [&]() -> int {  // next work item (uniform over the block)
-        const int q = pass++;
-        if (!p.counter) return q == 0 ? (int)blockIdx.x : p.n_items;
-        if (tid == 0) s_item = atomicAdd(p.counter, 1);
-        __syncthreads();
-        return s_item;
+    auto take = [&]() -> int { return p.counter ? atomicAdd(p.counter, 1) : n_items; };
+    auto issue_desc = [&](int slot, int idx) {
+        if (tid < 2 && idx < n_items)
+            cp_async16(reinterpret_cast<float*>(&s_d[slot]) + 4 * tid,
+                       reinterpret_cast<const float*>(p.items + idx) + 4 * tid);
+    };
+    auto issue_consts = [&](const BpItem& it, int a0) {
+        const int nac = min(kBpChunk, it.na - a0);
+        if (tid < 4 * nac)
+            cp_async16(reinterpret_cast<float*>(&s_k[tid >> 2]) + 4 * (tid & 3),
+                       reinterpret_cast<const float*>(p.bk + it.ang0 + a0 + (tid >> 2)) + 4 * (tid & 3));
+    };
+    auto setup = [&](const BpItem& it, int a0, int slot) {
+        if (tid < min(kBpChunk, it.na - a0)) {
+            bp_tile_angle(s_a[slot][tid], s_k[tid], it.tx * kBpTileX, it.ty * kBpTileY);
+            s_row[slot][tid] = p.sino + ((size_t)it.sinb + s_k[tid].row) * B;
+        }
     };
 
-    int cur_it = fetch();
-    if (cur_it >= p.n_items) return;
-    BpItem cur = p.items[cur_it];
-    int a0 = 0, buf = 0;
-    bp_chunk_setup(sa[0], p, cur, 0, tid);
+    // prologue: queue indices of items 0..2 (and 3, held by thread 0), their
+    // descriptors, constants and windows of chunk 0, constants of chunk 1
+    int pending = n_items;  // thread 0: queue index of the item three ahead of the current one
+    if (tid == 0) {
+        int q[3];
+        q[0] = p.counter ? atomicAdd(p.counter, 1) : (int)blockIdx.x;
+        q[1] = take();
+        q[2] = take();
+        pending = take();
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s_idx[i] = q[i];
+        s_idx[3] = n_items;
+    }
     __syncthreads();
-    bp_chunk_issue(wins, sa[0], min(kBpChunk, cur.na), B, tid);
+    if (s_idx[0] >= n_items) return;
+    for (int i = 0; i < 3; ++i) issue_desc(i, s_idx[i]);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    issue_consts(s_d[0], 0);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    setup(s_d[0], 0, 0);
+    __syncthreads();
+    int j = 0, a0 = 0, buf = 0;  // the current chunk: item ordinal j, first angle a0
+    {
+        const BpItem it = s_d[0];
+        bp_issue_windows(wins, s_a[0], s_row[0], min(kBpChunk, it.na), B, tid);
+        if (kBpChunk < it.na) issue_consts(it, kBpChunk);
+        else if (s_idx[1] < n_items) issue_consts(s_d[1], 0);
+        cp_async_commit();
+    }
+    int kiter = 0;
+    if (EPI == EPI_USTEP) kiter = *p.view.iter;
 
     float acc[4][4];
 #pragma unroll
@@ -538,37 +576,54 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
 
     for (;;) {
-        // the chunk after this one: the rest of this item, else the next item's first
-        int nxt_it = cur_it, na0 = a0 + kBpChunk;
-        if (na0 >= cur.na) {
-            nxt_it = fetch();
-            na0 = 0;
+        cp_async_wait<0>();
+        __syncthreads();  // (A) windows of this chunk, constants of the next, descriptors up to j + 2 landed
+        const BpItem cur = s_d[j & 3];
+        const int nac = min(kBpChunk, cur.na - a0);
+        // the next two chunks of the stream
+        int j1 = j, a1 = a0 + kBpChunk;
+        if (a1 >= cur.na) {
+            j1 = j + 1;
+            a1 = 0;
         }
-        const bool more = nxt_it < p.n_items;
-        BpItem nxt = cur;
-        if (more) {
-            if (nxt_it != cur_it) nxt = p.items[nxt_it];
-            bp_chunk_setup(sa[buf ^ 1], p, nxt, na0, tid);
-            __syncthreads();
-            bp_chunk_issue(wins + (buf ^ 1) * kBpStageFloat2, sa[buf ^ 1], min(kBpChunk, nxt.na - na0), B, tid);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        const bool v1 = s_idx[j1 & 3] < n_items;
+        const BpItem it1 = s_d[j1 & 3];
+        int j2 = j1, a2 = a1 + kBpChunk;
+        if (v1 && a2 >= it1.na) {
+            j2 = j1 + 1;
+            a2 = 0;
         }
+        const bool v2 = v1 && s_idx[j2 & 3] < n_items;
         if (!p.prescaled) {  // fold h into the pairs this thread copied (its own copies have landed)
-            float2* w = wins + buf * kBpStageFloat2;
-            const int nac = min(kBpChunk, cur.na - a0);
-            for (int e = tid; e < nac * kBpWin; e += kBpThreads) {
-                const float h = sa[buf][e / kBpWin].h;
-                const float2 v = w[e];
-                w[e] = make_float2(h * v.x, h * v.y);
+            for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
+                const float h = s_a[buf][a].h;
+                float2* w = wins + buf * kBpStageFloat2 + a * kBpWin;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float2 v = w[(tid & 31) + 32 * q];
+                    w[(tid & 31) + 32 * q] = make_float2(h * v.x, h * v.y);
+                }
             }
         }
-        __syncthreads();  // every thread's copies of this chunk have landed
+        if (v1) setup(it1, a1, buf ^ 1);
+        __syncthreads();  // (B) the next chunk's angles are set; the constants slot is free
+        if (v1) bp_issue_windows(wins + (buf ^ 1) * kBpStageFloat2, s_a[buf ^ 1], s_row[buf ^ 1],
+                                 min(kBpChunk, it1.na - a1), B, tid);
+        if (v2) issue_consts(s_d[j2 & 3], a2);
+        if (a0 == 0 && tid < 32) {  // a new item: the descriptor three items ahead, one more queue index
+            const int slot = (j + 3) & 3;
+            int idx = 0;
+            if (tid == 0) {
+                idx = pending;  // taken one item ago, so the queue's latency is hidden
+                s_idx[slot] = idx;
+                pending = idx < n_items ? take() : n_items;
+            }
+            issue_desc(slot, __shfl_sync(0xffffffffu, idx, 0));
+        }
+        cp_async_commit();
 
         const float2* win = wins + buf * kBpStageFloat2;
-        const BpAngle* sab = sa[buf];
-        const int nac = min(kBpChunk, cur.na - a0);
+        const BpAngle* sab = s_a[buf];
         for (int a = 0; a < nac; ++a) {
             const BpAngle& A = sab[a];
             const float2* wa = win + a * kBpWin;
@@ -593,7 +648,6 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         }
 
         if (a0 + kBpChunk >= cur.na) {  // the item's last chunk: epilogue
-
             const int x0 = cur.tx * kBpTileX, y0 = cur.ty * kBpTileY;
             if (EPI == EPI_STORE) {
                 float* img = p.img + (size_t)cur.img * n;
@@ -610,35 +664,50 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     }
                 }
             } else {
-                // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
+                // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k).
+                // Each row's view of x is located first (independent table lookups for
+                // the 4 rows).
                 const BpView& V = p.view;
-                const int k = *V.iter;
                 const float eta = V.eta1[cur.node];
                 float* u = V.u + (size_t)cur.img * n;
                 const float* lam = V.lam + (size_t)cur.img * n;
+                const float* xrow[4];
+#pragma unroll
+                for (int ky = 0; ky < 4; ++ky) {
+                    const int row = min(y0 + ty + 16 * ky, N - 1);
+                    const int mi = cur.node * V.M + V.seg_of_row[row];
+                    const int jj = kiter - V.lag[mi];
+                    xrow[ky] = jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +
+                                             (size_t)row * N
+                                       : nullptr;
+                }
+                // per row: the 12 loads first, then the updates and stores (a store to u
+                // may alias a later load, so loads are not moved past stores by the compiler)
 #pragma unroll
                 for (int ky = 0; ky < 4; ++ky) {
                     const int row = y0 + ty + 16 * ky;
                     if (row >= N) continue;
-                    const int seg = V.seg_of_row[row];
-                    const int mi = cur.node * V.M + seg;
-                    const int j = k - V.lag[mi];
-                    const float* xv = nullptr;
-                    if (j >= 1)
-                        xv = V.hist + ((((size_t)(j % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +
-                             (size_t)row * N;
+                    float* ur = u + (size_t)row * N;
+                    const float* lr = lam + (size_t)row * N;
+                    const float* xr = xrow[ky];
+                    float uo[4], lo[4], xo[4];
 #pragma unroll
                     for (int kx = 0; kx < 4; ++kx) {
                         const int col = x0 + tx + 16 * kx;
-                        if (col >= N) continue;
-                        const size_t o = (size_t)row * N + col;
-                        const float uo = u[o];
-                        const float x = xv ? xv[col] : 0.f;
-                        const float g = acc[ky][kx] + V.rho * (uo - x) + lam[o];
-                        acc[ky][kx] = uo - eta * g;
-                        u[o] = acc[ky][kx];
+                        const bool ok = col < N;
+                        uo[kx] = ok ? ur[col] : 0.f;
+                        lo[kx] = ok ? __ldg(lr + col) : 0.f;
+                        xo[kx] = (ok && xr) ? __ldg(xr + col) : 0.f;
+                    }
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx) {
+                        const int col = x0 + tx + 16 * kx;
+                        const float g = acc[ky][kx] + V.rho * (uo[kx] - xo[kx]) + lo[kx];
+                        acc[ky][kx] = uo[kx] - eta * g;
+                        if (col < N) ur[col] = acc[ky][kx];
                     }
                 }
+
                 if (V.uT) {  // the transposed copy read by the projector's steep-ray items
                     // 64 x 65 floats in this chunk's stage, free once every thread is done with it
                     float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
@@ -662,13 +731,12 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
 #pragma unroll
                 for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
         }
-        __syncthreads();  // this stage and sa[buf] are refilled two chunks on
-        if (!more) break;
-        cur = nxt;
-        cur_it = nxt_it;
-        a0 = na0;
+        if (!v1) break;
+        j = j1;
+        a0 = a1;
         buf ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // out[k][j][i] = in[k][i][j] for nimg images of N x N
@@ -937,6 +1005,15 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
     }
 }
 
+std::vector<BpConst> bp_list_consts(const Geometry& g, const std::vector<AngRow>& angs) {
+    std::vector<BpConst> out(angs.size());
+    for (size_t q = 0; q < angs.size(); ++q) {
+        out[q] = g.hb[angs[q].angle];
+        out[q].row = angs[q].row;
+    }
+    return out;
+}
+
 void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb, int node,
                     int slice, std::vector<BpItem>& out) {
     const int ntx = ceil_div(g.N, kBpTileX), nty = ceil_div(g.N, kBpTileY);
@@ -1053,18 +1130,15 @@ tomo_status tomo_geometry_create(int N, int n_bins, int n_angles, const double* 
             pt[a] = make_proj_angle(N, n_bins, c, s);
             bt[a] = make_bp_const(N, n_bins, c, s);
         }
+        g->hb = std::move(bt);
         cudaError_t e = cudaGetDevice(&g->device);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_ptab, sizeof(ProjAngle) * n_angles);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_btab, sizeof(BpConst) * n_angles);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int) * 4);
         if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int) * 4);
         if (e == cudaSuccess)
             e = cudaMemcpy(g->d_ptab, pt.data(), sizeof(ProjAngle) * n_angles, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g->d_btab, bt.data(), sizeof(BpConst) * n_angles, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(g->d_ptab);
-            cudaFree(g->d_btab);
             cudaFree(g->d_status);
             delete g;
             fail(TOMO_ERR_CUDA, std::string("tomo_geometry_create: ") + cudaGetErrorString(e));
@@ -1081,9 +1155,9 @@ tomo_status tomo_geometry_destroy(tomo_geometry_t gh) {
             cudaFree(s.d_angs);
             cudaFree(s.d_pitems);
             cudaFree(s.d_bitems);
+            cudaFree(s.d_bk);
         }
         cudaFree(g->d_ptab);
-        cudaFree(g->d_btab);
         cudaFree(g->d_status);
         delete g;
     });
@@ -1115,6 +1189,7 @@ static Geometry::Sel& selection(Geometry& g, const int32_t* angle_idx, int n_sel
         build_bp_items(g, 0, n_sel, k, k * n_sel, 0, 0, bi);
     }
     s.d_angs = device_upload(angs);
+    s.d_bk = device_upload(bp_list_consts(g, angs));
     s.d_pitems = device_upload(pi);
     s.n_pitems = (int)pi.size();
     s.d_bitems = device_upload(bi);
@@ -1123,6 +1198,7 @@ static Geometry::Sel& selection(Geometry& g, const int32_t* angle_idx, int n_sel
         cudaFree(g.cache.front().d_angs);
         cudaFree(g.cache.front().d_pitems);
         cudaFree(g.cache.front().d_bitems);
+        cudaFree(g.cache.front().d_bk);
         g.cache.erase(g.cache.begin());
     }
     g.cache.push_back(s);
@@ -1176,9 +1252,8 @@ tomo_status tomo_backproject(tomo_geometry_t gh, const float* sino, float* img, 
         p.sino = sino;
         p.img = img;
         p.items = s.d_bitems;
-        p.angs = s.d_angs;
+        p.bk = s.d_bk;
         p.n_items = s.n_bitems;
-        p.btab = g->d_btab;
         p.N = g->N;
         p.B = g->B;
         p.prescaled = 0;

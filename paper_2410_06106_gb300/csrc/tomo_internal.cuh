@@ -88,13 +88,14 @@ struct ProjItem {
 
 // backprojector work item: one 64 x 64 pixel tile of one image, all the
 // angles of an AngRow run
-struct BpItem {
+struct __align__(16) BpItem {
     int img;   // image index (units of N*N floats); also the u/lambda index in dADMM
-    int sinb;  // sinogram row base (added to AngRow::row)
+    int sinb;  // sinogram row base (added to BpConst::row)
     int tx, ty;
     int ang0, na;
     int node, slice;  // dADMM epilogue only
 };
+static_assert(sizeof(BpItem) == 32, "BpItem is copied in 16-byte pieces");
 
 constexpr int kProjThreads = 256;
 constexpr int kProjRows = 32;    // rows per staged chunk (the TMA box height)
@@ -131,21 +132,25 @@ struct ProjAngle {
 };
 
 // backprojector: pixel (i, j) sits at bin coordinate j C - i S + K (2^-40);
-// weights of its two candidate bins sat(wf0 - gam F), sat(wf1 + gam F)
-struct BpConst {
+// weights of its two candidate bins sat(wf0 - gam F), sat(wf1 + gam F).
+// Work lists carry one entry per (angle, sinogram row) of their angle list,
+// 64 bytes, so that a chunk's entries are copied with 16-byte cp.async.
+struct __align__(16) BpConst {
     long long C, S, K;
     int C25, S25;    // cos, sin in 2^-25: the steps of one pixel in x and y
     float gam;       // 1 / min(|c|, |s|) (capped at 2^20)
     float wf0, wf1;
     float h;         // 1 / max(|c|, |s|)
-    int pad[2];
+    int row;         // sinogram line of this entry (relative to the item's line base)
+    int pad[3];
 };
+static_assert(sizeof(BpConst) == 64, "BpConst is copied in 16-byte pieces");
 
 struct Geometry {
     int N = 0, B = 0, A = 0;
     int device = -1;
     ProjAngle* d_ptab = nullptr;  // [A] projector constants
-    BpConst* d_btab = nullptr;    // [A] backprojector constants
+    std::vector<BpConst> hb;      // [A] backprojector constants (host; lists copy from here)
     int* d_status = nullptr;  // device status word of standalone operator calls (bit 4: a wait gave up)
     std::vector<double> c, s;
     // cached device work lists of standalone project/backproject calls
@@ -153,6 +158,7 @@ struct Geometry {
         std::vector<int32_t> key;
         int batch = 0;
         AngRow* d_angs = nullptr;
+        BpConst* d_bk = nullptr;  // backprojector constants of the selection, in its order
         ProjItem* d_pitems = nullptr;
         int n_pitems = 0;
         BpItem* d_bitems = nullptr;
@@ -165,6 +171,9 @@ struct Geometry {
 // host: true when the rows of the image are the major (iteration) axis of
 // rays at this angle, i.e. |cos| >= |sin| (same test as the device)
 inline bool rows_major(double c, double s) { return std::abs(c) >= std::abs(s); }
+
+// host: the backprojector constants of an angle list, in its order
+std::vector<BpConst> bp_list_consts(const Geometry& g, const std::vector<AngRow>& angs);
 
 // host builders of work lists (operators.cu)
 void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int ang_begin,
@@ -215,9 +224,8 @@ struct BpParams {
     const float* sino;  // lines r_a, or h_a r_a when prescaled (the projector's prescaled output)
     float* img;         // EPI_STORE target
     const BpItem* items;
-    const AngRow* angs;
-    const BpConst* btab;
-    int* counter;
+    const BpConst* bk;    // constants of the items' angle list (BpItem::ang0 indexes it)
+    int* counter;         // persistent work queue; null: block b takes item b only
     int* status;
     int n_items;
     int N, B;
