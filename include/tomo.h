@@ -274,6 +274,14 @@ typedef struct {
 TOMO_API size_t dadmm_state_size(dadmm_t h); /* bytes of u+lam+xseg+hist+iter, for sizing */
 TOMO_API tomo_status dadmm_state_init(dadmm_t h, const dadmm_state* st, tomo_stream_t stream);
 
+/* Report that the caller wrote the state (u, lambda, x, history or the
+ * iteration counter) other than through dadmm_step / dadmm_state_init, e.g.
+ * when restoring a checkpoint. The library keeps a transposed copy of u in
+ * the workspace (read by the projector for steep rays) and rebuilds it at the
+ * next dadmm_step only after this call, after dadmm_state_init, or when the
+ * state or workspace pointers change. Host-only; never fails for a valid h. */
+TOMO_API tomo_status dadmm_state_modified(dadmm_t h);
+
 /* Scratch for dadmm_step (residuals, codec scratch, partial sums); device,
  * caller-owned, at least dadmm_workspace_size() bytes, 256-byte aligned. */
 TOMO_API size_t dadmm_workspace_size(dadmm_t h);

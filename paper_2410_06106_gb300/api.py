@@ -72,6 +72,7 @@ SIGNATURES = {
     "dadmm_state_size": (C.c_size_t, [C.c_void_p]),
     "dadmm_state_init": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p]),
     "dadmm_workspace_size": (C.c_size_t, [C.c_void_p]),
+    "dadmm_state_modified": (C.c_int, [C.c_void_p]),
     "dadmm_step": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_int, C.c_void_p,
                              C.c_size_t, C.c_void_p, C.c_void_p]),
     "dadmm_home_view": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_void_p]),
@@ -385,12 +386,14 @@ class DADMM:
     def load_state_dict(self, sd):
         for name in ("u", "lam", "xseg", "hist", "iter"):
             getattr(self, name).copy_(sd[name])
+        _check(lib().dadmm_state_modified(self.handle))
 
     def load_state(self, u, lam, xseg, hist, k):
         """set the state from arrays (numpy or torch) in the oracle's layout"""
         for name, v in (("u", u), ("lam", lam), ("xseg", xseg), ("hist", hist)):
             getattr(self, name).copy_(torch.as_tensor(np.asarray(v, np.float32)))
         self.iter.fill_(int(k))
+        _check(lib().dadmm_state_modified(self.handle))
 
     def reconstruct(self, sino_host, n_iters):
         """End-to-end call: host sinograms in, host reconstruction out.

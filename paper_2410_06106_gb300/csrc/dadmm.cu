@@ -75,6 +75,10 @@ struct Dadmm {
     size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_dual = 0,
            off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
     const void* ws_status_init = nullptr;  // workspace whose status word this handle has zeroed
+    // the transposed copy of u in the workspace is current for (ut_u, ut_ws) unless ut_dirty
+    const void* ut_u = nullptr;
+    const void* ut_ws = nullptr;
+    bool ut_dirty = true;
     // TMA descriptors of u and of its transposed copy (rebuilt with the graph)
     CUtensorMap map_u{}, map_uT{};
     int has_maps = 0;
@@ -952,7 +956,12 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
         TOMO_CUDA(cudaMemsetAsync(st->xseg, 0, sizeof(float) * h.S * n, s));
         TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * (size_t)h.D * 3 * h.S * n, s));
         TOMO_CUDA(cudaMemsetAsync(st->iter, 0, sizeof(int32_t), s));
+        h.ut_dirty = true;
     });
+}
+
+tomo_status dadmm_state_modified(dadmm_t hh) {
+    return guard([&] { as_dadmm(hh)->ut_dirty = true; });
 }
 
 tomo_status dadmm_sync_status(dadmm_t hh, void* workspace, size_t workspace_bytes, tomo_stream_t stream) {
@@ -1007,8 +1016,9 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
             TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), user));
             h.ws_status_init = workspace;
         }
-        // TMA descriptors of u and u^T; u^T is refreshed from u at every call (the state may
-        // have been set from outside), then kept in step by the u-step epilogue
+        // TMA descriptors of u and u^T; u^T is rebuilt from u when the state or the
+        // workspace changed (or the caller reported writing u), then kept in step by the
+        // u-step epilogue
         const bool maps = make_image_map(&h.map_u, st->u, h.N, h.S * h.M) &&
                           make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
         if (maps != (h.has_maps != 0) && h.gexec) {
@@ -1016,7 +1026,12 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
             h.gexec = nullptr;
         }
         h.has_maps = maps ? 1 : 0;
-        if (maps) launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
+        if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
+            launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
+            h.ut_u = st->u;
+            h.ut_ws = workspace;
+            h.ut_dirty = false;
+        }
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
                                                   w.resid};
