@@ -118,6 +118,8 @@ static BpConst make_bp_const(int N, int B, double c, double s) {
     r.K = std::llrint((hB - hN * c + hN * s) * kFix);
     r.C25 = (int)std::llrint(c * kFix25);
     r.S25 = (int)std::llrint(s * kFix25);
+    r.CX16 = (int)std::llrint(16.0 * c * kFix25);
+    r.SY16 = (int)std::llrint(16.0 * s * kFix25);
     const double gam = mn > 0.0 ? 1.0 / mn : (double)kGammaCap;
     r.gam = (float)gam;
     r.wf0 = (float)(0.5 + gam * (0.5 * mx + 1.0));
@@ -133,6 +135,7 @@ struct __align__(16) BpAngle {
     int w0;         // first staged bin of this tile
     float gam, wf0, wf1;
     float h;        // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
+    int CX16, SY16; // steps of 16 pixels, rounded once (not 16 rounded single steps)
 };
 
 // tile origin (x0, y0), tile extent kBpTileX x kBpTileY: the lowest bin
@@ -150,6 +153,8 @@ __device__ __forceinline__ void bp_tile_angle(BpAngle& r, const BpConst& k, int 
     r.wf0 = k.wf0;
     r.wf1 = k.wf1;
     r.h = k.h;
+    r.CX16 = k.CX16;
+    r.SY16 = k.SY16;
 }
 
 // asynchronous 4-byte global -> shared copy; zero-fill when !valid
@@ -630,7 +635,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
             // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
             const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
-            const unsigned cx = (unsigned)A.C25 << 4, sy = (unsigned)A.S25 << 4;
+            const unsigned cx = (unsigned)A.CX16, sy = (unsigned)A.SY16;
 #pragma unroll
             for (int ky = 0; ky < 4; ++ky) {
                 const unsigned prow = pb - (unsigned)ky * sy;

@@ -142,7 +142,8 @@ struct __align__(16) BpConst {
     float wf0, wf1;
     float h;         // 1 / max(|c|, |s|)
     int row;         // sinogram line of this entry (relative to the item's line base)
-    int pad[3];
+    int CX16, SY16;  // steps of 16 pixels in x and y, rounded once (2^-25)
+    int pad;
 };
 static_assert(sizeof(BpConst) == 64, "BpConst is copied in 16-byte pieces");
 
