@@ -129,32 +129,39 @@ static BpConst make_bp_const(int N, int B, double c, double s) {
 }
 
 // one angle of a backprojector chunk, for the chunk's tile
+// (32 bytes: the inner loop reads it with two 16-byte shared loads)
 struct __align__(16) BpAngle {
     unsigned P0;    // bin coordinate of the tile's first pixel minus w0 (2^-25)
     int C25, S25;   // steps of one pixel in x and y (2^-25)
-    int w0;         // first staged bin of this tile
     float gam, wf0, wf1;
-    float h;        // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
     int CX16, SY16; // steps of 16 pixels, rounded once (not 16 rounded single steps)
+};
+
+// what the copies of a chunk's windows need per angle
+struct BpWin {
+    const float* row;  // sinogram line
+    int w0;            // first staged bin of this tile
+    float h;           // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
 };
 
 // tile origin (x0, y0), tile extent kBpTileX x kBpTileY: the lowest bin
 // coordinate over the tile is at the corner picked by the signs of C and S
-__device__ __forceinline__ void bp_tile_angle(BpAngle& r, const BpConst& k, int x0, int y0) {
+__device__ __forceinline__ void bp_tile_angle(BpAngle& r, BpWin& wv, const BpConst& k, int x0, int y0) {
     const long long j = x0 + (k.C < 0 ? kBpTileX - 1 : 0);
     const long long i = y0 + (k.S > 0 ? kBpTileY - 1 : 0);
     const long long lo = j * k.C - i * k.S + k.K;
-    r.w0 = (int)(lo >> 40) - 2;
+    const int w0 = (int)(lo >> 40) - 2;
     const long long org = (long long)x0 * k.C - (long long)y0 * k.S + k.K;
-    r.P0 = (unsigned)((org - ((long long)r.w0 << 40)) >> (40 - kFracBits));
+    r.P0 = (unsigned)((org - ((long long)w0 << 40)) >> (40 - kFracBits));
     r.C25 = k.C25;
     r.S25 = k.S25;
     r.gam = k.gam;
     r.wf0 = k.wf0;
     r.wf1 = k.wf1;
-    r.h = k.h;
     r.CX16 = k.CX16;
     r.SY16 = k.SY16;
+    wv.w0 = w0;
+    wv.h = k.h;
 }
 
 // asynchronous 4-byte global -> shared copy; zero-fill when !valid
@@ -476,13 +483,12 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // asynchronous copies of a chunk's windows: win[a][k] = (r[w0 + k], r[w0 + k + 1])
 // of the line, zero outside [0, B); warp w takes angles w, w + 8, ...
-__device__ __forceinline__ void bp_issue_windows(float2* win, const BpAngle* sa, const float* const* rows, int nac,
-                                                 int B, int tid) {
+__device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, int nac, int B, int tid) {
     static_assert(kBpWin == 96, "three pairs per lane");
     const int lane = tid & 31;
     for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
-        const int w0 = sa[a].w0;
-        const float* row = rows[a];
+        const int w0 = wv[a].w0;
+        const float* row = wv[a].row;
         float* d = reinterpret_cast<float*>(win + a * kBpWin);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -510,7 +516,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
     float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][kBpChunk][kBpWin]
     __shared__ BpConst s_k[kBpChunk];                  // constants of the chunk after next
     __shared__ BpAngle s_a[2][kBpChunk];               // this chunk and the next, for their tiles
-    __shared__ const float* s_row[2][kBpChunk];
+    __shared__ BpWin s_w[2][kBpChunk];
     __shared__ BpItem s_d[4];                          // descriptors of the block's items j .. j + 3
     __shared__ int s_idx[4];                           // their queue indices (>= n_items: none)
     const int tid = threadIdx.x;
@@ -533,8 +539,8 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
     };
     auto setup = [&](const BpItem& it, int a0, int slot) {
         if (tid < min(kBpChunk, it.na - a0)) {
-            bp_tile_angle(s_a[slot][tid], s_k[tid], it.tx * kBpTileX, it.ty * kBpTileY);
-            s_row[slot][tid] = p.sino + ((size_t)it.sinb + s_k[tid].row) * B;
+            bp_tile_angle(s_a[slot][tid], s_w[slot][tid], s_k[tid], it.tx * kBpTileX, it.ty * kBpTileY);
+            s_w[slot][tid].row = p.sino + ((size_t)it.sinb + s_k[tid].row) * B;
         }
     };
 
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
     int j = 0, a0 = 0, buf = 0;  // the current chunk: item ordinal j, first angle a0
     {
         const BpItem it = s_d[0];
-        bp_issue_windows(wins, s_a[0], s_row[0], min(kBpChunk, it.na), B, tid);
+        bp_issue_windows(wins, s_w[0], min(kBpChunk, it.na), B, tid);
         if (kBpChunk < it.na) issue_consts(it, kBpChunk);
         else if (s_idx[1] < n_items) issue_consts(s_d[1], 0);
         cp_async_commit();
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         const bool v2 = v1 && s_idx[j2 & 3] < n_items;
         if (!p.prescaled) {  // fold h into the pairs this thread copied (its own copies have landed)
             for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
-                const float h = s_a[buf][a].h;
+                const float h = s_w[buf][a].h;
                 float2* w = wins + buf * kBpStageFloat2 + a * kBpWin;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
@@ -612,8 +618,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         }
         if (v1) setup(it1, a1, buf ^ 1);
         __syncthreads();  // (B) the next chunk's angles are set; the constants slot is free
-        if (v1) bp_issue_windows(wins + (buf ^ 1) * kBpStageFloat2, s_a[buf ^ 1], s_row[buf ^ 1],
-                                 min(kBpChunk, it1.na - a1), B, tid);
+        if (v1) bp_issue_windows(wins + (buf ^ 1) * kBpStageFloat2, s_w[buf ^ 1], min(kBpChunk, it1.na - a1), B, tid);
         if (v2) issue_consts(s_d[j2 & 3], a2);
         if (a0 == 0 && tid < 32) {  // a new item: the descriptor three items ahead, one more queue index
             const int slot = (j + 3) & 3;
