@@ -40,6 +40,10 @@ def lib():
             "orc_dct8x8": (None, [p, p]),
             "orc_idct8x8": (None, [p, p]),
             "orc_jpeg": (i64, [p, i32, i32, i32, p, p, p]),
+            "orc_jpeg_entropy": (i64, [p, i64, p]),
+            "orc_jpeg_entropy_decode": (i32, [p, i64, i64, p]),
+            "orc_huff_code": (None, [i32, i32, p, p]),
+            "orc_zigzag": (None, [p]),
             "orc_relay_tables": (None, [i32, p, p, p]),
             "orc_dadmm_iterate": (i32, [i32, i32, i32, i32, i32, p, p, p, p, p, p, p, p,
                                         d, p, d, i32, i32, i32, i32, i32, u64, i32,
@@ -191,6 +195,38 @@ def jpeg(v, quality):
     deq = np.empty_like(v)
     nnz = lib().orc_jpeg(_ptr(v), rows, cols, int(quality), _ptr(coefs), _ptr(lohi), _ptr(deq))
     return coefs, lohi, deq, int(nnz)
+
+
+def jpeg_entropy(coefs):
+    """baseline Huffman-coded bytes (stuffed, padded) of quantized blocks [nblk, 64]"""
+    c = np.ascontiguousarray(coefs, np.int16).reshape(-1, 64)
+    n = lib().orc_jpeg_entropy(_ptr(c), len(c), None)
+    if n < 0:
+        raise ValueError("coefficient outside the baseline range")
+    out = np.empty(max(n, 1), np.uint8)
+    lib().orc_jpeg_entropy(_ptr(c), len(c), _ptr(out))
+    return out[:n].tobytes()
+
+
+def jpeg_entropy_decode(data, nblk):
+    buf = np.frombuffer(bytes(data), np.uint8).copy()
+    out = np.empty((nblk, 64), np.int16)
+    if lib().orc_jpeg_entropy_decode(_ptr(buf), len(buf), int(nblk), _ptr(out)) != 0:
+        raise ValueError("malformed entropy-coded segment")
+    return out
+
+
+def huff_code(ac, symbol):
+    """(code, length) of a DC category (ac=False) or AC run/size symbol"""
+    code, ln = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    lib().orc_huff_code(int(bool(ac)), int(symbol), _ptr(code), _ptr(ln))
+    return int(code[0]), int(ln[0])
+
+
+def zigzag():
+    zz = np.empty(64, np.int32)
+    lib().orc_zigzag(_ptr(zz))
+    return zz
 
 
 def relay_tables(adj):

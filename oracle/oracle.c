@@ -363,6 +363,232 @@ void orc_idct8x8(const double* in, double* out) {
         }
 }
 
+/* ---------------------------------------------------------------------
+ * Baseline sequential Huffman coding of quantized 8x8 blocks (ITU-T T.81,
+ * Annex F.1.2: DC differences by category + extra bits, AC run/size
+ * symbols with ZRL and EOB, zig-zag order of Figure A.6), with the example
+ * luminance tables of Annex K (Table K.3: DC, Table K.5: AC), the canonical
+ * code assignment of Annex C, byte stuffing (a 0x00 after every 0xFF,
+ * F.1.2.3) and padding of the last byte with 1-bits.
+ * ------------------------------------------------------------------- */
+static const uint8_t K3_BITS[16] = {0, 1, 5, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0};
+static const uint8_t K3_VALS[12] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+static const uint8_t K5_BITS[16] = {0, 2, 1, 3, 3, 2, 4, 3, 5, 5, 4, 4, 0, 0, 1, 125};
+static const uint8_t K5_VALS[162] = {
+    0x01, 0x02, 0x03, 0x00, 0x04, 0x11, 0x05, 0x12, 0x21, 0x31, 0x41, 0x06, 0x13, 0x51, 0x61, 0x07,
+    0x22, 0x71, 0x14, 0x32, 0x81, 0x91, 0xa1, 0x08, 0x23, 0x42, 0xb1, 0xc1, 0x15, 0x52, 0xd1, 0xf0,
+    0x24, 0x33, 0x62, 0x72, 0x82, 0x09, 0x0a, 0x16, 0x17, 0x18, 0x19, 0x1a, 0x25, 0x26, 0x27, 0x28,
+    0x29, 0x2a, 0x34, 0x35, 0x36, 0x37, 0x38, 0x39, 0x3a, 0x43, 0x44, 0x45, 0x46, 0x47, 0x48, 0x49,
+    0x4a, 0x53, 0x54, 0x55, 0x56, 0x57, 0x58, 0x59, 0x5a, 0x63, 0x64, 0x65, 0x66, 0x67, 0x68, 0x69,
+    0x6a, 0x73, 0x74, 0x75, 0x76, 0x77, 0x78, 0x79, 0x7a, 0x83, 0x84, 0x85, 0x86, 0x87, 0x88, 0x89,
+    0x8a, 0x92, 0x93, 0x94, 0x95, 0x96, 0x97, 0x98, 0x99, 0x9a, 0xa2, 0xa3, 0xa4, 0xa5, 0xa6, 0xa7,
+    0xa8, 0xa9, 0xaa, 0xb2, 0xb3, 0xb4, 0xb5, 0xb6, 0xb7, 0xb8, 0xb9, 0xba, 0xc2, 0xc3, 0xc4, 0xc5,
+    0xc6, 0xc7, 0xc8, 0xc9, 0xca, 0xd2, 0xd3, 0xd4, 0xd5, 0xd6, 0xd7, 0xd8, 0xd9, 0xda, 0xe1, 0xe2,
+    0xe3, 0xe4, 0xe5, 0xe6, 0xe7, 0xe8, 0xe9, 0xea, 0xf1, 0xf2, 0xf3, 0xf4, 0xf5, 0xf6, 0xf7, 0xf8,
+    0xf9, 0xfa};
+
+typedef struct {
+    uint16_t code[256];
+    uint8_t len[256]; /* 0: no code for this symbol */
+} huff_table;
+
+/* Annex C: codes of each length are consecutive; the first code of length
+ * l + 1 is (the code after the last one of length l) shifted left by one */
+static void huff_build(const uint8_t* bits, const uint8_t* vals, huff_table* t) {
+    memset(t, 0, sizeof(*t));
+    uint32_t code = 0;
+    int k = 0;
+    for (int l = 1; l <= 16; ++l) {
+        for (int i = 0; i < bits[l - 1]; ++i, ++k) {
+            t->code[vals[k]] = (uint16_t)code++;
+            t->len[vals[k]] = (uint8_t)l;
+        }
+        code <<= 1;
+    }
+}
+
+void orc_huff_code(int ac, int symbol, int32_t* code, int32_t* len) {
+    huff_table t;
+    if (ac) huff_build(K5_BITS, K5_VALS, &t);
+    else huff_build(K3_BITS, K3_VALS, &t);
+    *code = t.code[symbol & 255];
+    *len = t.len[symbol & 255];
+}
+
+/* zig-zag position k -> natural index (row * 8 + column): the anti-diagonals
+ * i + j = d in turn, downwards on odd d, upwards on even d (Figure A.6) */
+void orc_zigzag(int32_t* zz) {
+    int k = 0;
+    for (int d = 0; d < 15; ++d) {
+        const int ilo = d < 8 ? 0 : d - 7, ihi = d < 8 ? d : 7;
+        if (d & 1)
+            for (int i = ilo; i <= ihi; ++i) zz[k++] = i * 8 + (d - i);
+        else
+            for (int i = ihi; i >= ilo; --i) zz[k++] = i * 8 + (d - i);
+    }
+}
+
+typedef struct {
+    uint8_t* out;
+    int64_t n;
+    uint32_t acc;
+    int nacc;
+} bit_writer;
+
+static void put_bit(bit_writer* w, unsigned bit) {
+    w->acc = (w->acc << 1) | (bit & 1u);
+    if (++w->nacc == 8) {
+        const uint8_t b = (uint8_t)w->acc;
+        if (w->out) w->out[w->n] = b;
+        w->n++;
+        if (b == 0xFF) { /* byte stuffing */
+            if (w->out) w->out[w->n] = 0x00;
+            w->n++;
+        }
+        w->acc = 0;
+        w->nacc = 0;
+    }
+}
+
+static void put_bits(bit_writer* w, uint32_t v, int len) {
+    for (int i = len - 1; i >= 0; --i) put_bit(w, (v >> i) & 1u);
+}
+
+/* magnitude category (Tables F.1 / F.2) and its extra bits (F.1.2.1.1) */
+static int category(int v) {
+    int a = v < 0 ? -v : v, s = 0;
+    while (a) {
+        ++s;
+        a >>= 1;
+    }
+    return s;
+}
+
+static uint32_t extra_bits(int v, int s) {
+    return (uint32_t)(v >= 0 ? v : v - 1) & ((1u << s) - 1u);
+}
+
+int64_t orc_jpeg_entropy(const int16_t* coefs, int64_t nblk, uint8_t* out) {
+    huff_table dc, ac;
+    huff_build(K3_BITS, K3_VALS, &dc);
+    huff_build(K5_BITS, K5_VALS, &ac);
+    int32_t zz[64];
+    orc_zigzag(zz);
+    bit_writer w = {out, 0, 0, 0};
+    int pred = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        const int16_t* c = coefs + b * 64;
+        const int diff = c[0] - pred;
+        pred = c[0];
+        const int sd = category(diff);
+        if (sd > 11) return -1;
+        put_bits(&w, dc.code[sd], dc.len[sd]);
+        put_bits(&w, extra_bits(diff, sd), sd);
+        int run = 0;
+        for (int k = 1; k < 64; ++k) {
+            const int v = c[zz[k]];
+            if (v == 0) {
+                ++run;
+                continue;
+            }
+            while (run > 15) {
+                put_bits(&w, ac.code[0xF0], ac.len[0xF0]);
+                run -= 16;
+            }
+            const int sa = category(v);
+            if (sa > 10) return -1;
+            const int sym = (run << 4) | sa;
+            put_bits(&w, ac.code[sym], ac.len[sym]);
+            put_bits(&w, extra_bits(v, sa), sa);
+            run = 0;
+        }
+        if (run > 0) put_bits(&w, ac.code[0x00], ac.len[0x00]); /* EOB */
+    }
+    while (w.nacc != 0) put_bit(&w, 1u); /* pad with 1-bits */
+    return w.n;
+}
+
+/* decoder (Annex F.2.2), for the round-trip check: returns 0, or -1 on a
+ * malformed stream */
+typedef struct {
+    const uint8_t* in;
+    int64_t n, pos;
+    uint32_t acc;
+    int nacc;
+} bit_reader;
+
+static int get_bit(bit_reader* r) {
+    if (r->nacc == 0) {
+        if (r->pos >= r->n) return -1;
+        const uint8_t b = r->in[r->pos++];
+        if (b == 0xFF) {
+            if (r->pos >= r->n || r->in[r->pos] != 0x00) return -1;
+            r->pos++; /* the stuffed zero */
+        }
+        r->acc = b;
+        r->nacc = 8;
+    }
+    r->nacc--;
+    return (int)((r->acc >> r->nacc) & 1u);
+}
+
+static int decode_symbol(bit_reader* r, const huff_table* t) {
+    uint32_t code = 0;
+    for (int l = 1; l <= 16; ++l) {
+        const int bit = get_bit(r);
+        if (bit < 0) return -1;
+        code = (code << 1) | (uint32_t)bit;
+        for (int s = 0; s < 256; ++s)
+            if (t->len[s] == l && t->code[s] == code) return s;
+    }
+    return -1;
+}
+
+static int receive_extend(bit_reader* r, int s, int* v) {
+    uint32_t x = 0;
+    for (int i = 0; i < s; ++i) {
+        const int bit = get_bit(r);
+        if (bit < 0) return -1;
+        x = (x << 1) | (uint32_t)bit;
+    }
+    *v = (s == 0) ? 0 : ((x >> (s - 1)) ? (int)x : (int)x - (1 << s) + 1);
+    return 0;
+}
+
+int orc_jpeg_entropy_decode(const uint8_t* in, int64_t nbytes, int64_t nblk, int16_t* coefs) {
+    huff_table dc, ac;
+    huff_build(K3_BITS, K3_VALS, &dc);
+    huff_build(K5_BITS, K5_VALS, &ac);
+    int32_t zz[64];
+    orc_zigzag(zz);
+    bit_reader r = {in, nbytes, 0, 0, 0};
+    int pred = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        int16_t* c = coefs + b * 64;
+        memset(c, 0, sizeof(int16_t) * 64);
+        const int sd = decode_symbol(&r, &dc);
+        int diff;
+        if (sd < 0 || receive_extend(&r, sd, &diff)) return -1;
+        pred += diff;
+        c[0] = (int16_t)pred;
+        for (int k = 1; k < 64;) {
+            const int sym = decode_symbol(&r, &ac);
+            if (sym < 0) return -1;
+            if (sym == 0x00) break; /* EOB */
+            if (sym == 0xF0) {
+                k += 16;
+                continue;
+            }
+            k += sym >> 4;
+            if (k > 63) return -1;
+            int v;
+            if (receive_extend(&r, sym & 15, &v)) return -1;
+            c[zz[k++]] = (int16_t)v;
+        }
+    }
+    return 0;
+}
+
 int64_t orc_jpeg(const float* v, int rows, int cols, int quality,
                  int16_t* coefs, float* lohi, float* deq) {
     int32_t qt[64];
@@ -590,9 +816,11 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                     while ((1 << bits) < km_k) ++bits;
                     kind_bytes[q] = bits * (double)len / 8.0 + 4.0 * km_k;
                 } else {
-                    int64_t nnz = orc_jpeg(seg32, rows, N, jpeg_quality, coefs, lohi, deq32);
+                    orc_jpeg(seg32, rows, N, jpeg_quality, coefs, lohi, deq32);
                     for (long i = 0; i < len; ++i) dst[i] = deq32[i];
-                    kind_bytes[q] = 2.0 * (double)nnz + 8.0;
+                    /* the entropy-coded blocks + (lo, hi); a constant segment is sent as lo alone */
+                    const int64_t eb = (lohi[1] > lohi[0]) ? orc_jpeg_entropy(coefs, len / 64, NULL) : 0;
+                    kind_bytes[q] = (double)eb + 8.0;
                 }
             }
             for (int t = 0; t < M; ++t)

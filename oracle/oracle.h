@@ -86,6 +86,19 @@ void orc_idct8x8(const double* in, double* out);
 int64_t orc_jpeg(const float* v, int rows, int cols, int quality,
                  int16_t* coefs, float* lohi, float* deq);
 
+/* Baseline Huffman entropy coding of quantized blocks (ITU-T T.81 Annex
+ * F.1.2 with the luminance tables K.3 / K.5): coefs [nblk][64] in natural
+ * order, blocks in raster order (one DC predictor over the whole array).
+ * Returns the length in bytes of the entropy-coded segment (stuffed, padded
+ * with 1-bits), -1 if a coefficient is out of the baseline range; writes the
+ * bytes to out unless it is NULL. */
+int64_t orc_jpeg_entropy(const int16_t* coefs, int64_t nblk, uint8_t* out);
+int orc_jpeg_entropy_decode(const uint8_t* in, int64_t nbytes, int64_t nblk, int16_t* coefs);
+/* code word and length of a DC category (ac = 0) or AC run/size symbol (ac = 1) */
+void orc_huff_code(int ac, int symbol, int32_t* code, int32_t* len);
+/* zig-zag position -> natural index (Figure A.6) */
+void orc_zigzag(int32_t* zz);
+
 /* Relay tables of the message graph: dist[s*M+m] = hop distance from owner s
  * to node m (-1 if unreachable), first[s*M+m] = the neighbour of s on the
  * shortest path to m that always takes the lowest-id parent. */

@@ -150,3 +150,20 @@ def test_bytes_follow_the_communication_model():
     st = O.DADMM(p, oracle_eta1(p))
     stats = st.iterate(p["sino"])
     assert stats[0, 4] == 4.0 * M * (M - 1) * (N * N // M)
+
+
+def test_jpeg_bytes_are_the_entropy_coded_messages():
+    """complete graph, JPEG messages: each owner's segment reaches the M - 1
+    others as its baseline Huffman-coded blocks plus (lo, hi), 8 bytes"""
+    N, M, quality = 32, 4, 60
+    p = small_problem(N=N, A=24, B=47, M=M, graph="complete", quant="jpeg", jpeg_quality=quality, noise=0.02)
+    st = O.DADMM(p, oracle_eta1(p))
+    stats = st.iterate(p["sino"])
+    seg = p["seg_row_ptr"]
+    want = 0.0
+    for m in range(M):
+        x = st.xseg[0, seg[m]:seg[m + 1]].astype(np.float32)  # the owner's segment after Algorithm 3
+        coefs, lohi, _, _ = O.jpeg(x, quality)
+        eb = len(O.jpeg_entropy(coefs)) if lohi[1] > lohi[0] else 0
+        want += (M - 1) * (eb + 8)
+    assert stats[0, 4] == want
