@@ -360,7 +360,11 @@ def run_ours(args, ws, rank, local):
                "sample": "one Algorithm 2 inner step of nodes 0..%d of slice 0 (%.3g updates, %.1f s)"
                          % (args.cpu_nodes - 1, cu, ct)}
 
-    launches_per_iter = 2 * E1 + 6
+    # our kernels per batched iteration: E1 x (projector, backprojector), x-step, K-means and
+    # JPEG (+ its entropy coder) when those messages exist, dual, residual norm, finalize
+    kinds = set(np.asarray(prob["home_q"]).tolist()) | set(
+        np.asarray(prob["edge_q"])[np.asarray(prob["adj"]) > 0].tolist())
+    launches_per_iter = 2 * E1 + 4 + (1 in kinds) + 2 * (2 in kinds)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "iters_per_s": 1e3 / ms_max,

@@ -203,6 +203,28 @@ TOMO_API uint64_t quant_kmeans_key(uint64_t seed, int slice, int owner, int iter
 TOMO_API tomo_status quant_jpeg(const float* in, int rows, int cols, int quality, int16_t* coefs,
                        float* lohi, float* deq, int64_t* nnz, tomo_stream_t stream);
 
+/* Baseline sequential Huffman coding of the quantized blocks of one image
+ * (ITU-T T.81 Annex F.1.2: DC differences by category with extra bits, AC
+ * run/size symbols with ZRL and EOB in the zig-zag order of Figure A.6),
+ * with the luminance tables of Annex K (Table K.3 DC, Table K.5 AC), codes
+ * assigned as in Annex C, one DC predictor over the image, the last byte
+ * padded with 1-bits and a 0x00 stuffed after every 0xFF byte: the
+ * entropy-coded segment of a single-component baseline scan.
+ *   coefs [rows/8][cols/8][64] int16, device, natural order within a block
+ *     (the layout quant_jpeg writes); |AC| <= 1023, |DC difference| <= 2047;
+ *   stream: device buffer of stream_cap >= quant_jpeg_entropy_bound() bytes
+ *     for the stuffed segment, or NULL to count only;
+ *   nbytes: device int64, set to the segment's length in bytes, or to -1 when
+ *     a coefficient is outside the baseline range (nothing meaningful is
+ *     written then);
+ *   workspace: device scratch of quant_jpeg_entropy_workspace_size() bytes.
+ * Asynchronous on `stream_`; one CTA codes the image. */
+TOMO_API size_t quant_jpeg_entropy_bound(int rows, int cols);
+TOMO_API size_t quant_jpeg_entropy_workspace_size(int rows, int cols);
+TOMO_API tomo_status quant_jpeg_entropy(const int16_t* coefs, int rows, int cols, uint8_t* stream,
+                                        size_t stream_cap, int64_t* nbytes, void* workspace,
+                                        size_t workspace_bytes, tomo_stream_t stream_);
+
 /* ------------------------------------------------------------------ */
 /* Decentralized ADMM with quantized messages (Sec. 2.4-2.7, Alg. 2-4)  */
 /* ------------------------------------------------------------------ */

@@ -66,6 +66,10 @@ SIGNATURES = {
     "quant_kmeans_key": (C.c_uint64, [C.c_uint64, C.c_int, C.c_int, C.c_int]),
     "quant_jpeg": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.c_void_p]),
+    "quant_jpeg_entropy_bound": (C.c_size_t, [C.c_int, C.c_int]),
+    "quant_jpeg_entropy_workspace_size": (C.c_size_t, [C.c_int, C.c_int]),
+    "quant_jpeg_entropy": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                     C.c_void_p, C.c_size_t, C.c_void_p]),
     "dadmm_create": (C.c_int, [C.c_void_p, C.POINTER(DadmmConfig), C.c_void_p]),
     "dadmm_destroy": (C.c_int, [C.c_void_p]),
     "dadmm_ring_depth": (C.c_int, [C.c_void_p]),
@@ -242,6 +246,28 @@ def quant_jpeg(x, quality):
     _check(lib().quant_jpeg(_ptr(x), rows, cols, int(quality), _ptr(coefs), _ptr(lohi), _ptr(deq), _ptr(nnz),
                             _stream()))
     return coefs, lohi, deq, nnz
+
+
+def jpeg_entropy(coefs, rows, cols, stream=True):
+    """Baseline Huffman entropy-coded segment of quantized blocks [nblk, 64]
+    (CUDA int16, natural order, blocks in raster order of a rows x cols
+    image). Returns the stuffed stream as bytes (stream=True) or its length"""
+    if not torch.cuda.is_available():
+        raise TomoError(-2, "no CUDA device: libtomo has no CPU path")
+    if not coefs.is_cuda or coefs.dtype != torch.int16 or coefs.numel() != (rows // 8) * (cols // 8) * 64:
+        raise TomoError(-1, "expected int16 CUDA coefficients [rows/8 * cols/8, 64]")
+    coefs = coefs.contiguous()
+    lib_ = lib()
+    ws = torch.empty(lib_.quant_jpeg_entropy_workspace_size(rows, cols), dtype=torch.uint8, device=coefs.device)
+    cap = lib_.quant_jpeg_entropy_bound(rows, cols)
+    out = torch.empty(cap, dtype=torch.uint8, device=coefs.device) if stream else None
+    n = torch.empty(1, dtype=torch.int64, device=coefs.device)
+    _check(lib_.quant_jpeg_entropy(_ptr(coefs), rows, cols, _ptr(out), cap if stream else 0, _ptr(n),
+                                   _ptr(ws), ws.numel(), _stream()))
+    nb = int(n.item())
+    if nb < 0:
+        raise TomoError(-1, "coefficient outside the baseline JPEG range")
+    return out[:nb].cpu().numpy().tobytes() if stream else nb
 
 
 def lincomb(xs, coefs, out=None):

@@ -507,7 +507,6 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCod
     const SegTask T = p.tasks[task_begin + blockIdx.y];
     const int N = p.N, bpr = N / 8;
     const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
-    int c = 0;
     if (blk < ((T.r1 - T.r0) / 8) * bpr) {
         const int kk = *p.iter;
         const size_t n = (size_t)N * N;
@@ -517,14 +516,260 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCod
         float* dst = p.hist + ((size_t)slot * 3 + DADMM_Q_JPEG) * p.S * n + o;
         const float lo = key_float(p.lo_key[T.slice * p.M + T.owner]);
         const float hi = key_float(p.hi_key[T.slice * p.M + T.owner]);
-        if (hi > lo)
-            c = jpeg_block(p.xseg + o, dst, N, lo, hi, qt, nullptr, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
-        else
+        int16_t* cf = p.coefs + ((size_t)T.blk0 + blk) * 64;
+        if (hi > lo) {
+            jpeg_block(p.xseg + o, dst, N, lo, hi, qt, cf, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
+        } else {
             jpeg_const_block(dst, N, lo);
+            for (int e = 0; e < 64; ++e) cf[e] = 0;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c)
-        atomicAdd((unsigned long long*)(p.nnz + T.slice * p.M + T.owner), (unsigned long long)c);
+}
+
+// ---------------------------------------------------------------------------
+// Baseline Huffman entropy coding of quantized 8x8 blocks (ITU-T T.81 Annex
+// F.1.2: DC difference categories + extra bits, AC run/size symbols with ZRL
+// and EOB in zig-zag order) with the luminance tables of Annex K (K.3 DC,
+// K.5 AC), codes assigned canonically (Annex C). One CTA per image: the
+// blocks' bit lengths are scanned across the CTA 256 blocks at a time, every
+// thread packs its block's codes at its bit offset into a zeroed word
+// buffer (stream bit 0 = the MSB of word 0; atomicOr where two blocks share
+// a word), the last byte is padded with 1-bits, and every 0xFF byte is
+// followed by a stuffed 0x00 (counted; written when a stream is requested).
+// ---------------------------------------------------------------------------
+namespace {
+const uint8_t kDcBits[16] = {0, 1, 5, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0};
+const uint8_t kAcBits[16] = {0, 2, 1, 3, 3, 2, 4, 3, 5, 5, 4, 4, 0, 0, 1, 125};
+const uint8_t kAcVals[162] = {
+    0x01, 0x02, 0x03, 0x00, 0x04, 0x11, 0x05, 0x12, 0x21, 0x31, 0x41, 0x06, 0x13, 0x51, 0x61, 0x07, 0x22, 0x71,
+    0x14, 0x32, 0x81, 0x91, 0xa1, 0x08, 0x23, 0x42, 0xb1, 0xc1, 0x15, 0x52, 0xd1, 0xf0, 0x24, 0x33, 0x62, 0x72,
+    0x82, 0x09, 0x0a, 0x16, 0x17, 0x18, 0x19, 0x1a, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2a, 0x34, 0x35, 0x36, 0x37,
+    0x38, 0x39, 0x3a, 0x43, 0x44, 0x45, 0x46, 0x47, 0x48, 0x49, 0x4a, 0x53, 0x54, 0x55, 0x56, 0x57, 0x58, 0x59,
+    0x5a, 0x63, 0x64, 0x65, 0x66, 0x67, 0x68, 0x69, 0x6a, 0x73, 0x74, 0x75, 0x76, 0x77, 0x78, 0x79, 0x7a, 0x83,
+    0x84, 0x85, 0x86, 0x87, 0x88, 0x89, 0x8a, 0x92, 0x93, 0x94, 0x95, 0x96, 0x97, 0x98, 0x99, 0x9a, 0xa2, 0xa3,
+    0xa4, 0xa5, 0xa6, 0xa7, 0xa8, 0xa9, 0xaa, 0xb2, 0xb3, 0xb4, 0xb5, 0xb6, 0xb7, 0xb8, 0xb9, 0xba, 0xc2, 0xc3,
+    0xc4, 0xc5, 0xc6, 0xc7, 0xc8, 0xc9, 0xca, 0xd2, 0xd3, 0xd4, 0xd5, 0xd6, 0xd7, 0xd8, 0xd9, 0xda, 0xe1, 0xe2,
+    0xe3, 0xe4, 0xe5, 0xe6, 0xe7, 0xe8, 0xe9, 0xea, 0xf1, 0xf2, 0xf3, 0xf4, 0xf5, 0xf6, 0xf7, 0xf8, 0xf9, 0xfa};
+// zig-zag position -> natural index (row * 8 + column)
+const uint8_t kZigzag[64] = {0,  1,  8,  16, 9,  2,  3,  10, 17, 24, 32, 25, 18, 11, 4,  5,
+                             12, 19, 26, 33, 40, 48, 41, 34, 27, 20, 13, 6,  7,  14, 21, 28,
+                             35, 42, 49, 56, 57, 50, 43, 36, 29, 22, 15, 23, 30, 37, 44, 51,
+                             58, 59, 52, 45, 38, 31, 39, 46, 53, 60, 61, 54, 47, 55, 62, 63};
+}  // namespace
+
+struct HuffTables {
+    uint32_t dc[12];   // (code << 8) | length of each DC category
+    uint32_t ac[256];  // (code << 8) | length of each run/size symbol (length 0: none)
+    uint8_t zz[64];
+};
+
+static const HuffTables& huff_tables() {
+    static HuffTables t;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        std::memset(&t, 0, sizeof(t));
+        auto build = [](const uint8_t* bits, const uint8_t* vals, uint32_t* out) {
+            uint32_t code = 0;
+            int k = 0;
+            for (int l = 1; l <= 16; ++l) {
+                for (int i = 0; i < bits[l - 1]; ++i, ++k) out[vals ? vals[k] : k] = (code++ << 8) | (uint32_t)l;
+                code <<= 1;
+            }
+        };
+        build(kDcBits, nullptr, t.dc);
+        build(kAcBits, kAcVals, t.ac);
+        std::memcpy(t.zz, kZigzag, 64);
+    });
+    return t;
+}
+
+struct EntropyTask {
+    long long blk0;   // first block in the coefficient buffer
+    long long word0;  // first word of the bit buffer (kEntropyWordsPerBlock per block)
+    int nblk;
+    int out;          // index of the byte count to write
+    int lohi;         // >= 0: index of the (lo, hi) keys; a constant segment codes to 0 bytes
+    int pad;
+};
+
+struct EntropyParams {
+    HuffTables t;
+    const int16_t* coefs;
+    EntropyTask one;      // the task when seg is null (standalone call: one CTA)
+    const SegTask* seg;   // dADMM: one CTA per JPEG segment
+    uint32_t* bits;
+    long long* bytes;     // out: stream length in bytes (stuffed), -1 if a coefficient is out of range
+    const unsigned* lo_key;
+    const unsigned* hi_key;
+    uint8_t* stream;      // optional: the stuffed stream (single task)
+    int N, M;             // dADMM: image width, nodes
+};
+
+__device__ __forceinline__ uint32_t extra_bits(int v, int s) {
+    return (uint32_t)(v >= 0 ? v : v - 1) & ((1u << s) - 1u);
+}
+
+__device__ __forceinline__ int category(int v) { return 32 - __clz(v < 0 ? -v : v); }
+
+// codes of one block as (value, length) pairs, value = code word then extra bits;
+// returns false if a coefficient is outside the baseline range
+template <class Emit>
+__device__ __forceinline__ bool code_block(const int16_t* c, int pred, const uint32_t* dc, const uint32_t* ac,
+                                           const uint8_t* zz, Emit emit) {
+    const int diff = c[0] - pred;
+    const int sd = category(diff);
+    if (sd > 11) return false;
+    emit(((dc[sd] >> 8) << sd) | extra_bits(diff, sd), (int)(dc[sd] & 255u) + sd);
+    int run = 0;
+    for (int k = 1; k < 64; ++k) {
+        const int v = c[zz[k]];
+        if (v == 0) {
+            ++run;
+            continue;
+        }
+        for (; run > 15; run -= 16) emit(ac[0xF0] >> 8, (int)(ac[0xF0] & 255u));
+        const int sa = category(v);
+        if (sa > 10) return false;
+        const uint32_t a = ac[(run << 4) | sa];
+        emit(((a >> 8) << sa) | extra_bits(v, sa), (int)(a & 255u) + sa);
+        run = 0;
+    }
+    if (run) emit(ac[0] >> 8, (int)(ac[0] & 255u));  // EOB
+    return true;
+}
+
+// stream bits [o, o + len) = the low len bits of v, MSB first (len <= 27)
+__device__ __forceinline__ void put_bits(uint32_t* buf, unsigned long long o, uint32_t v, int len) {
+    const unsigned long long x = (unsigned long long)v << (64 - (int)(o & 31) - len);
+    atomicOr(buf + (o >> 5), (uint32_t)(x >> 32));
+    if ((uint32_t)x) atomicOr(buf + (o >> 5) + 1, (uint32_t)x);
+}
+
+// CTA-wide exclusive scan of one value per thread (256 threads); returns the
+// prefix and sets *total
+__device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* total) {
+    __shared__ long long s_w[kJpegThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    long long before = 0, all = 0;
+    for (int w = 0; w < kJpegThreads / 32; ++w) {
+        if (w < warp) before += s_w[w];
+        all += s_w[w];
+    }
+    __syncthreads();  // s_w reused by the next call
+    *total = all;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kJpegThreads) jpeg_entropy_kernel(const __grid_constant__ EntropyParams p) {
+    __shared__ uint32_t s_dc[12], s_ac[256];
+    __shared__ uint8_t s_zz[64];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 256; i += kJpegThreads) s_ac[i] = p.t.ac[i];
+    if (tid < 12) s_dc[tid] = p.t.dc[tid];
+    if (tid < 64) s_zz[tid] = p.t.zz[tid];
+    if (tid == 0) s_bad = 0;
+    EntropyTask T;
+    if (p.seg) {
+        const SegTask S = p.seg[blockIdx.x];
+        T.blk0 = S.blk0;
+        T.word0 = S.word0;
+        T.nblk = ((S.r1 - S.r0) / 8) * (p.N / 8);
+        T.out = S.slice * p.M + S.owner;
+        T.lohi = T.out;
+    } else {
+        T = p.one;
+    }
+    __syncthreads();
+    if (T.lohi >= 0 && !(key_float(p.hi_key[T.lohi]) > key_float(p.lo_key[T.lohi]))) {
+        if (tid == 0) p.bytes[T.out] = 0;  // a constant segment is sent as its value alone
+        return;
+    }
+    uint32_t* buf = p.bits + T.word0;
+    const long long nwords = (long long)T.nblk * kEntropyWordsPerBlock + 1;
+    for (long long i = tid; i < nwords; i += kJpegThreads) buf[i] = 0u;
+    __syncthreads();
+    const int16_t* coefs = p.coefs + T.blk0 * 64;
+    unsigned long long base = 0;
+    for (int b0 = 0; b0 < T.nblk; b0 += kJpegThreads) {
+        const int b = b0 + tid;
+        const bool mine = b < T.nblk;
+        const int pred = (mine && b > 0) ? coefs[(size_t)(b - 1) * 64] : 0;
+        int nbits = 0;
+        if (mine && !code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz,
+                                [&](uint32_t, int len) { nbits += len; }))
+            atomicOr(&s_bad, 1);
+        long long total;
+        const unsigned long long at = base + (unsigned long long)cta_exclusive_scan(nbits, &total);
+        if (mine) {
+            unsigned long long o = at;
+            code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz, [&](uint32_t v, int len) {
+                if (len > 0) put_bits(buf, o, v, len);
+                o += len;
+            });
+        }
+        base += (unsigned long long)total;
+    }
+    if (tid == 0 && (base & 7)) {  // pad the last byte with 1-bits
+        const int pad = 8 - (int)(base & 7);
+        put_bits(buf, base, (1u << pad) - 1u, pad);
+    }
+    __threadfence();
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) p.bytes[T.out] = -1;
+        return;
+    }
+    // 0xFF bytes of the stream, each followed by a stuffed zero
+    const unsigned long long nbytes = (base + 7) >> 3;
+    const long long nw = (long long)((nbytes + 3) >> 2);
+    unsigned long long out_pos = 0;
+    for (long long w0 = 0; w0 < nw; w0 += kJpegThreads) {
+        const long long w = w0 + tid;
+        uint32_t word = 0;
+        int nb = 0, ff = 0;
+        if (w < nw) {
+            word = __ldcg(buf + w);
+            nb = (int)min(4ull, nbytes - 4ull * (unsigned long long)w);
+            for (int q = 0; q < nb; ++q) ff += ((word >> (24 - 8 * q)) & 255u) == 255u;
+        }
+        long long total;
+        const long long before = cta_exclusive_scan(nb + ff, &total);
+        if (p.stream && w < nw) {
+            unsigned long long o = out_pos + before;
+            for (int q = 0; q < nb; ++q) {
+                const uint8_t byte = (uint8_t)(word >> (24 - 8 * q));
+                p.stream[o++] = byte;
+                if (byte == 255u) p.stream[o++] = 0;
+            }
+        }
+        out_pos += (unsigned long long)total;
+    }
+    if (tid == 0) p.bytes[T.out] = (long long)out_pos;
+}
+
+void launch_jpeg_entropy_dadmm(const DadmmCodec& c, int task_begin, int task_count, cudaStream_t st) {
+    if (task_count <= 0) return;
+    EntropyParams p{};
+    p.t = huff_tables();
+    p.coefs = c.coefs;
+    p.seg = c.tasks + task_begin;
+    p.bits = c.bits;
+    p.bytes = c.jbytes;
+    p.lo_key = c.lo_key;
+    p.hi_key = c.hi_key;
+    p.N = c.N;
+    p.M = c.M;
+    jpeg_entropy_kernel<<<task_count, kJpegThreads, 0, st>>>(p);
+    TOMO_CUDA(cudaGetLastError());
 }
 
 static float* lohi_scratch() {
@@ -588,6 +833,45 @@ tomo_status quant_kmeans(const float* in, int64_t n, int k, int iters, uint64_t 
         TOMO_REQUIRE(k >= 1 && k <= kKmMaxK, "k must be in [1, 32]");
         TOMO_REQUIRE(iters >= 0 && iters <= 10000, "iters out of range");
         launch_kmeans_single(in, n, k, iters, key, codes, centroids, deq, objective, (cudaStream_t)stream);
+    });
+}
+
+size_t quant_jpeg_entropy_bound(int rows, int cols) {
+    if (rows < 8 || cols < 8) return 0;
+    const size_t nblk = (size_t)(rows / 8) * (cols / 8);
+    return 2 * (nblk * kEntropyWordsPerBlock * 4 + 4);  // every byte stuffed, at worst
+}
+
+size_t quant_jpeg_entropy_workspace_size(int rows, int cols) {
+    if (rows < 8 || cols < 8) return 0;
+    const size_t nblk = (size_t)(rows / 8) * (cols / 8);
+    return (nblk * kEntropyWordsPerBlock + 1) * sizeof(uint32_t);
+}
+
+tomo_status quant_jpeg_entropy(const int16_t* coefs, int rows, int cols, uint8_t* stream, size_t stream_cap,
+                               int64_t* nbytes, void* workspace, size_t workspace_bytes, tomo_stream_t st) {
+    return guard([&] {
+        TOMO_REQUIRE(coefs && nbytes, "coefs and nbytes must be non-NULL");
+        TOMO_REQUIRE(rows >= 8 && cols >= 8 && rows % 8 == 0 && cols % 8 == 0,
+                     "rows and cols must be positive multiples of 8");
+        TOMO_REQUIRE(workspace && workspace_bytes >= quant_jpeg_entropy_workspace_size(rows, cols),
+                     "workspace too small");
+        TOMO_REQUIRE(((uintptr_t)workspace % 4) == 0, "workspace must be 4-byte aligned");
+        TOMO_REQUIRE(!stream || stream_cap >= quant_jpeg_entropy_bound(rows, cols),
+                     "stream capacity below quant_jpeg_entropy_bound()");
+        EntropyParams p{};
+        p.t = huff_tables();
+        p.coefs = coefs;
+        p.one.blk0 = 0;
+        p.one.word0 = 0;
+        p.one.nblk = (rows / 8) * (cols / 8);
+        p.one.out = 0;
+        p.one.lohi = -1;
+        p.bits = (uint32_t*)workspace;
+        p.bytes = (long long*)nbytes;
+        p.stream = stream;
+        jpeg_entropy_kernel<<<1, kJpegThreads, 0, (cudaStream_t)st>>>(p);
+        TOMO_CUDA(cudaGetLastError());
     });
 }
 

@@ -72,7 +72,7 @@ struct Dadmm {
     std::vector<int> km_index, jp_index;              // [(slice*M + owner)] -> task index or -1
     int grid_proj = 0, grid_bp = 0;
     // workspace layout (byte offsets from the aligned base)
-    size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_dual = 0,
+    size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_coefs = 0, off_bits = 0, off_dual = 0,
            off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
     const void* ws_status_init = nullptr;  // workspace whose status word this handle has zeroed
     // the transposed copy of u in the workspace is current for (ut_u, ut_ws) unless ut_dirty
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kElemThreads) resid_kernel(const float* resid,
 struct FinParams {
     const double* dual_part;
     const double* res_part;
-    const long long* nnz;      // [S][M]
+    const long long* nnz;      // [S][M] entropy-coded JPEG message bytes
     const int32_t* recv;       // [M][3]
     const int32_t* seg_rows;   // [M]
     double* stats;             // [kStatsCap][S][DADMM_NSTAT]
@@ -298,7 +298,7 @@ __global__ void finalize_kernel(const FinParams p) {
             const double len = (double)p.seg_rows[m] * p.N;
             by += p.recv[m * 3 + 0] * 4.0 * len;
             by += p.recv[m * 3 + 1] * (bits * len / 8.0 + 4.0 * p.km_k);
-            by += p.recv[m * 3 + 2] * (2.0 * (double)p.nnz[slice * p.M + m] + 8.0);
+            by += p.recv[m * 3 + 2] * ((double)p.nnz[slice * p.M + m] + 8.0);  // entropy-coded blocks + (lo, hi)
         }
         s[0][threadIdx.x] = a;
         s[1][threadIdx.x] = b;
@@ -454,7 +454,9 @@ struct WsPtrs {
     int* counters;
     unsigned* lo;
     unsigned* hi;
-    long long* nnz;
+    long long* nnz;      // [S][M] entropy-coded JPEG message bytes
+    int16_t* coefs;      // quantized blocks of the JPEG segments
+    uint32_t* bits;      // their entropy-coding bit buffers
     double* dual;
     double* res;
     double* stats;
@@ -470,6 +472,8 @@ static WsPtrs ws_ptrs(const Dadmm& h, void* ws) {
     w.lo = (unsigned*)(b + h.off_lo);
     w.hi = (unsigned*)(b + h.off_hi);
     w.nnz = (long long*)(b + h.off_nnz);
+    w.coefs = (int16_t*)(b + h.off_coefs);
+    w.bits = (uint32_t*)(b + h.off_bits);
     w.dual = (double*)(b + h.off_dual);
     w.res = (double*)(b + h.off_res);
     w.stats = (double*)(b + h.off_stats);
@@ -599,7 +603,9 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     cp.seed = h.seed;
     cp.lo_key = w.lo;
     cp.hi_key = w.hi;
-    cp.nnz = w.nnz;
+    cp.coefs = w.coefs;
+    cp.bits = w.bits;
+    cp.jbytes = w.nnz;
     cp.M = h.M;
     if (batched) {
         const int rows = h.S * h.N;
@@ -612,6 +618,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
         mark();
         cp.tasks = h.d_jp;
         launch_jpeg_dadmm(cp, h.jpeg_q, h.max_jp_rows, 0, h.n_jp, s);
+        launch_jpeg_entropy_dadmm(cp, 0, h.n_jp, s);
         mark();
         dual_kernel<<<dim3(h.M * kDualPerNode, h.S), kElemThreads, 0, s>>>(ep, 0, 0);
         TOMO_CUDA(cudaGetLastError());
@@ -635,7 +642,10 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
         for (int sl = 0; sl < h.S; ++sl)
             for (int m = 0; m < h.M; ++m) {
                 const int ji = h.jp_index[sl * h.M + m];
-                if (ji >= 0) launch_jpeg_dadmm(cp, h.jpeg_q, h.seg_row_ptr[m + 1] - h.seg_row_ptr[m], ji, 1, s);
+                if (ji >= 0) {
+                    launch_jpeg_dadmm(cp, h.jpeg_q, h.seg_row_ptr[m + 1] - h.seg_row_ptr[m], ji, 1, s);
+                    launch_jpeg_entropy_dadmm(cp, ji, 1, s);
+                }
             }
         mark();
         for (int sl = 0; sl < h.S; ++sl)
@@ -874,17 +884,21 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->d_mx = device_upload(mx);
             // codec tasks, slice-major
             std::vector<SegTask> km, jp;
+            long long jp_blocks = 0;
             h->km_index.assign((size_t)c.S * M, -1);
             h->jp_index.assign((size_t)c.S * M, -1);
             for (int sl = 0; sl < c.S; ++sl)
                 for (int m = 0; m < M; ++m) {
-                    const SegTask t{sl, m, h->seg_row_ptr[m], h->seg_row_ptr[m + 1]};
+                    SegTask t{sl, m, h->seg_row_ptr[m], h->seg_row_ptr[m + 1], 0, 0, 0};
                     if ((h->need[m] >> 1) & 1) {
                         h->km_index[(size_t)sl * M + m] = (int)km.size();
                         km.push_back(t);
                     }
                     if ((h->need[m] >> 2) & 1) {
                         h->jp_index[(size_t)sl * M + m] = (int)jp.size();
+                        t.blk0 = (int)jp_blocks;
+                        t.word0 = jp_blocks * kEntropyWordsPerBlock + (long long)jp.size();  // + 1 word each
+                        jp_blocks += (long long)((t.r1 - t.r0) / 8) * (N / 8);
                         jp.push_back(t);
                         h->max_jp_rows = std::max(h->max_jp_rows, t.r1 - t.r0);
                     }
@@ -911,6 +925,8 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->off_lo = take(sizeof(unsigned) * SMn);
             h->off_hi = take(sizeof(unsigned) * SMn);
             h->off_nnz = take(sizeof(long long) * SMn);
+            h->off_coefs = take(sizeof(int16_t) * 64 * (size_t)std::max(jp_blocks, 1LL));
+            h->off_bits = take(sizeof(uint32_t) * ((size_t)jp_blocks * kEntropyWordsPerBlock + jp.size() + 1));
             h->off_dual = take(sizeof(double) * 3 * SMn * kDualPerNode);
             h->off_res = take(sizeof(double) * (size_t)c.S * kResPerSlice);
             h->off_stats = take(sizeof(double) * (size_t)kStatsCap * c.S * DADMM_NSTAT);

@@ -272,7 +272,10 @@ constexpr int kKmProbes = 64;
 // by dadmm_create, read by the dADMM variants of the codec kernels
 struct SegTask {
     int slice, owner;
-    int r0, r1;  // rows of the segment
+    int r0, r1;        // rows of the segment
+    int blk0;          // JPEG: first of the segment's 8x8 blocks in the coefficient buffer
+    int pad;
+    long long word0;   // JPEG: first word of the segment's entropy-coding bit buffer
 };
 
 struct DadmmCodec {
@@ -286,9 +289,15 @@ struct DadmmCodec {
     // JPEG only
     const unsigned* lo_key;  // [S][M] order-preserving keys of the segment min / max
     const unsigned* hi_key;
-    long long* nnz;          // [S][M]
+    int16_t* coefs;          // quantized blocks of every task, natural order
+    uint32_t* bits;          // entropy-coding bit buffers of every task
+    long long* jbytes;       // [S][M] entropy-coded message bytes
     int M;
 };
+
+// worst case of the baseline entropy coder: 8x8 block = DC code + extra
+// (9 + 11 bits) + 63 AC codes + extra (16 + 10 bits), in 32-bit words
+constexpr int kEntropyWordsPerBlock = 52;
 
 void launch_kmeans_single(const float* in, long long n, int k, int iters, uint64_t key,
                           uint8_t* codes, float* cent, float* deq, double* obj, cudaStream_t st);
@@ -298,6 +307,7 @@ void launch_jpeg_single(const float* in, int rows, int cols, int quality, int16_
                         float* lohi, float* deq, long long* nnz, cudaStream_t st);
 void launch_jpeg_dadmm(const DadmmCodec& p, int quality, int max_rows, int task_begin,
                        int task_count, cudaStream_t st);
+void launch_jpeg_entropy_dadmm(const DadmmCodec& p, int task_begin, int task_count, cudaStream_t st);
 size_t kmeans_smem(int kmax);
 void jpeg_quant_table(int quality, int32_t* qt);  // host, natural order
 

@@ -117,3 +117,53 @@ def test_jpeg_rational_coefficient_tie():
     oc, _, odeq, _ = O.jpeg(seg, 55)
     assert coefs.cpu().numpy()[0, 32] == 2
     assert np.array_equal(coefs.cpu().numpy(), oc) and np.array_equal(deq.cpu().numpy(), odeq)
+
+
+def random_blocks(nblk, seed):
+    """Laplacian-like sparse quantized blocks over the whole baseline range"""
+    rng = np.random.default_rng(seed)
+    zz = O.zigzag()
+    c = np.zeros((nblk, 64), np.int16)
+    for b in range(nblk):
+        c[b, 0] = rng.integers(-1024, 1017)
+        k = int(rng.integers(0, 64))
+        pos = rng.choice(np.arange(1, 64), k, replace=False)
+        c[b, zz[pos]] = np.clip(np.round(rng.laplace(0, [1, 20, 300][b % 3], k)), -1023, 1023)
+    return c
+
+
+@pytest.mark.parametrize("rows,cols,seed", [(8, 8, 0), (16, 800, 1), (64, 64, 2), (256, 512, 3), (8, 2056, 4)])
+def test_entropy_coding_matches_oracle_bytewise(rows, cols, seed):
+    """the stuffed baseline entropy-coded segment, byte for byte (several
+    256-block batches in the larger cases)"""
+    need_gpu()
+    nblk = (rows // 8) * (cols // 8)
+    c = random_blocks(nblk, seed)
+    ref = O.jpeg_entropy(c)
+    got = api.jpeg_entropy(torch.as_tensor(c).cuda(), rows, cols)
+    assert got == ref
+    assert api.jpeg_entropy(torch.as_tensor(c).cuda(), rows, cols, stream=False) == len(ref)
+
+
+def test_entropy_coding_of_quantizer_output_and_stuffing():
+    """coefficients from the JPEG quantizer at several qualities, and a block
+    whose stream holds a stuffed 0xFF"""
+    need_gpu()
+    rng = np.random.default_rng(11)
+    x = np.cumsum(rng.standard_normal((64, 512)), axis=1).astype(np.float32)
+    for q in (10, 50, 75, 95):
+        coefs, _, _, _ = api.quant_jpeg(cuda(x), q)
+        assert api.jpeg_entropy(coefs, 64, 512) == O.jpeg_entropy(coefs.cpu().numpy())
+    c = np.zeros((2, 64), np.int16)
+    c[0, 0] = 1
+    c[0, O.zigzag()[16]] = 1000
+    data = api.jpeg_entropy(torch.as_tensor(c).cuda(), 8, 16)
+    assert b"\xff\x00" in data and data == O.jpeg_entropy(c)
+
+
+def test_entropy_coding_refuses_out_of_range_coefficients():
+    need_gpu()
+    c = np.zeros((1, 64), np.int16)
+    c[0, 1] = 1024
+    with pytest.raises(api.TomoError):
+        api.jpeg_entropy(torch.as_tensor(c).cuda(), 8, 8)

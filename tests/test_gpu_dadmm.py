@@ -66,12 +66,15 @@ def test_state_injection_small(quant, graph, M):
     sino = torch.as_tensor(p["sino"]).cuda()
     s.step(sino, 6)
     before = gpu_state(s)
-    s.step(sino, 1)
+    st = s.step(sino, 1)
     after = gpu_state(s)
     o = O.DADMM(p, eta)
     o.load_state(*before)
-    o.iterate(p["sino"])
+    ost = o.iterate(p["sino"])
     compare_states(after, o, p)
+    # bytes on the wire: exact sizes (K-means, identity) and entropy-coded JPEG messages,
+    # which a code at a rounding tie may change by a few bits
+    assert abs(st[0, :, 4] - ost[:, 4]).max() <= 1e-3 * ost[:, 4].max()
 
 
 @pytest.mark.parametrize("name", ["c2_kmeans", "c3_batch_jpeg"])
