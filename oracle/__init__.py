@@ -47,7 +47,7 @@ def lib():
             "orc_relay_tables": (None, [i32, p, p, p]),
             "orc_dadmm_iterate": (i32, [i32, i32, i32, i32, i32, p, p, p, p, p, p, p, p,
                                         d, p, d, i32, i32, i32, i32, i32, u64, i32,
-                                        p, p, p, p, p, p, p]),
+                                        p, p, p, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -261,7 +261,10 @@ class DADMM:
         self.home_q = _i32(prob["home_q"])
         self.eta1 = _f64(eta1)
         dist, _ = relay_tables(self.adj)
-        self.D = max(1, int(dist.max())) + 1  # max relay lag + 2
+        self.max_stale = int(prob.get("max_stale", 0))
+        self.D = max(1, int(dist.max())) + 1 + self.max_stale  # max relay lag + 2 + staleness allowed
+        self.lag = np.where(np.eye(self.M, dtype=bool), 0, dist - 1).astype(np.int32)  # [s, m]
+        self.held = None  # versions held [s, m] once messages may be lost
         N, M, S = self.N, self.M, self.S
         self.u = np.zeros((S, M, N, N))
         self.lam = np.zeros((S, M, N, N))
@@ -277,12 +280,16 @@ class DADMM:
         assert self.hist.shape[0] == self.D
         self.k = int(k)
 
-    def iterate(self, sino):
-        """one iteration on sinograms [S, A, B]; returns stats [S, NSTAT]"""
+    def iterate(self, sino, drop=None):
+        """one iteration on sinograms [S, A, B]; returns stats [S, NSTAT].
+        drop [M, M] (s, m): node m loses owner s's message in this exchange"""
         p = self.p
         d = _f64(sino)
         it = np.array([self.k], np.int32)
         stats = np.empty((self.S, NSTAT), np.float64)
+        if drop is not None and self.held is None:  # the versions every node holds without losses
+            self.held = np.maximum(self.k - self.lag, 0).astype(np.int32)
+        dr = None if drop is None else np.ascontiguousarray(drop, np.uint8)
         rc = lib().orc_dadmm_iterate(
             self.N, self.B, self.A, self.S, self.M, _ptr(self.c), _ptr(self.s),
             _ptr(self.node_ang_ptr), _ptr(self.node_ang), _ptr(self.seg_row_ptr),
@@ -290,7 +297,7 @@ class DADMM:
             float(p["rho"]), _ptr(self.eta1), float(p["eta2"]), int(p["E1"]), int(p["E2"]),
             int(p["km_k"]), int(p["km_iters"]), int(p["jpeg_quality"]), int(p["seed"]),
             self.D, _ptr(d), _ptr(self.u), _ptr(self.lam), _ptr(self.xseg), _ptr(self.hist),
-            _ptr(it), _ptr(stats))
+            _ptr(it), _ptr(stats), None if dr is None else _ptr(dr), None if self.held is None else _ptr(self.held))
         if rc != 0:
             raise ValueError("orc_dadmm_iterate failed: %d" % rc)
         self.k = int(it[0])

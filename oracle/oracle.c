@@ -695,6 +695,12 @@ typedef struct {
     const double* hist;
 } view_ctx;
 
+/* relay lag of segment s at node m: one hop per iteration, the first hop is
+ * the exchange of the iteration itself */
+static int relay_lag(const view_ctx* v, int s, int m) {
+    return (s == m) ? 0 : v->dist[(long)s * v->M + m] - 1;
+}
+
 /* quantizer of the message that carries segment s to node m */
 static int msg_kind(const view_ctx* v, int s, int m) {
     if (s == m) return v->home_q[m];
@@ -704,13 +710,13 @@ static int msg_kind(const view_ctx* v, int s, int m) {
 
 /* node m's copy of x after k completed iterations: segment s holds the
  * message produced at iteration k - max(dist(s,m) - 1, 0) (one relay hop per
- * iteration), or the initial zero if that message does not exist yet */
-static void build_view(const view_ctx* v, int slice, int m, int k, double* out) {
+ * iteration), or, when `held` is given, the version held[s*M+m] that node m
+ * last received (messages can be lost); version 0 is the initial zero */
+static void build_view(const view_ctx* v, int slice, int m, int k, const int32_t* held, double* out) {
     const long n = (long)v->N * v->N;
     for (int s = 0; s < v->M; ++s) {
         const long r0 = (long)v->seg_row_ptr[s] * v->N, r1 = (long)v->seg_row_ptr[s + 1] * v->N;
-        int lag = (s == m) ? 0 : v->dist[(long)s * v->M + m] - 1;
-        int j = k - lag;
+        int j = held ? held[(long)s * v->M + m] : k - relay_lag(v, s, m);
         if (j < 1) {
             for (long i = r0; i < r1; ++i) out[i] = 0.0;
             continue;
@@ -729,7 +735,8 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       double rho, const double* eta1, double eta2, int E1, int E2,
                       int km_k, int km_iters, int jpeg_quality, uint64_t seed,
                       int D, const double* sino, double* u, double* lam,
-                      double* xseg, double* hist, int32_t* iter, double* stats) {
+                      double* xseg, double* hist, int32_t* iter, double* stats,
+                      const uint8_t* drop, int32_t* held) {
     const long n = (long)N * N;
     if (N <= 0 || B <= 0 || M <= 0 || S <= 0 || D <= 0 || km_k > 256) return -1;
     if (seg_row_ptr[0] != 0 || seg_row_ptr[M] != N) return -1;
@@ -747,6 +754,25 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
 
     view_ctx vc = {N, M, D, S, seg_row_ptr, dist, first, edge_q, home_q, hist};
     const int k = *iter;
+    /* message versions held after this iteration: every node receives the newest
+     * version that has reached it (k + 1 - lag) unless drop[s*M+m] says that
+     * message was lost, in which case it keeps the one it holds; its own
+     * segment is never lost. Every version read must still be in the ring. */
+    int32_t* held1 = NULL;
+    if (held) {
+        held1 = (int32_t*)malloc(sizeof(int32_t) * M * M);
+        for (int s_ = 0; s_ < M; ++s_)
+            for (int m = 0; m < M; ++m) {
+                const long i = (long)s_ * M + m;
+                const int newest = k + 1 - relay_lag(&vc, s_, m);
+                const int lost = drop && s_ != m && drop[i];
+                held1[i] = (!lost && newest >= 1) ? newest : held[i];
+                const int ok_u = held[i] < 1 || held[i] >= k + 1 - D;                    /* read by Alg. 2 */
+                const int ok_d = held1[i] < 1 || held1[i] >= k + 2 - D;                  /* read by Eq. 24 */
+                const int ok_c = m != 0 || held[i] < 1 || held[i] >= k + 2 - D;          /* change statistic */
+                if (!(ok_u && ok_d && ok_c)) { free(held1); free(dist); free(first); return -4; }
+            }
+    }
     double* xv = (double*)malloc(sizeof(double) * n);
     double* xv0 = (double*)malloc(sizeof(double) * n);
     double* g = (double*)malloc(sizeof(double) * n);
@@ -767,7 +793,7 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
             double* lm = lam + ((long)sl * M + m) * n;
             const int na = node_ang_ptr[m + 1] - node_ang_ptr[m];
             const int32_t* ang = node_ang + node_ang_ptr[m];
-            build_view(&vc, sl, m, k, xv); /* x_m^k */
+            build_view(&vc, sl, m, k, held, xv); /* x_m^k */
             for (int e = 0; e < E1; ++e) {
                 orc_project(N, B, c, s, na, ang, 1, um, r); /* P_m u_m */
                 for (int q = 0; q < na; ++q)
@@ -832,9 +858,9 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
         for (int m = 0; m < M; ++m) {
             const double* um = u + ((long)sl * M + m) * n;
             double* lm = lam + ((long)sl * M + m) * n;
-            build_view(&vc, sl, m, k + 1, xv); /* x_m^{k+1} */
+            build_view(&vc, sl, m, k + 1, held1, xv); /* x_m^{k+1} */
             if (m == 0) {
-                build_view(&vc, sl, 0, k, xv0);
+                build_view(&vc, sl, 0, k, held, xv0);
                 for (long i = 0; i < n; ++i) {
                     chg2 += (xv[i] - xv0[i]) * (xv[i] - xv0[i]);
                     nrm2 += xv0[i] * xv0[i];
@@ -854,6 +880,10 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
         st[4] = bytes;
     }
     *iter = k + 1;
+    if (held) {
+        memcpy(held, held1, sizeof(int32_t) * M * M);
+        free(held1);
+    }
     free(xv); free(xv0); free(g); free(r); free(seg32); free(deq32); free(codes); free(coefs);
     free(dist); free(first);
     return 0;

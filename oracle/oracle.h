@@ -114,6 +114,10 @@ void orc_relay_tables(int M, const int32_t* adj, int32_t* dist, int32_t* first);
 
 /* One dADMM iteration (Algorithm 4 with Algorithms 2, 3 and Eq. 21-24) for
  * S independent slices of M nodes each. See oracle.c for the step list.
+ * Lost messages: held [M][M] (NULL: none are lost) is the version of owner
+ * s's segment that node m holds (held[s*M+m], 0 = none yet), read for x_m^k
+ * and updated to x_m^{k+1}; drop [M][M] (NULL: none lost this iteration)
+ * marks the messages lost in this iteration's exchange, for every slice.
  *   sino  [S][A][B]          measured data, natural angle order
  *   u,lam [S][M][N*N]        local images and duals (updated)
  *   xseg  [S][N*N]           every owner's unquantized segment (updated)
@@ -121,7 +125,8 @@ void orc_relay_tables(int M, const int32_t* adj, int32_t* dist, int32_t* first);
  *                            D >= max(hop distance) + 1
  *   iter  in: completed iterations k; out: k+1
  *   stats [S][ORC_NSTAT]
- * Returns 0, or a negative code for invalid arguments. */
+ * Returns 0, a negative code for invalid arguments, or -4 when a held
+ * version has left the message ring (depth D). */
 int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       const double* c, const double* s,
                       const int32_t* node_ang_ptr, const int32_t* node_ang,
@@ -131,7 +136,8 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       double rho, const double* eta1, double eta2, int E1, int E2,
                       int km_k, int km_iters, int jpeg_quality, uint64_t seed,
                       int D, const double* sino, double* u, double* lam,
-                      double* xseg, double* hist, int32_t* iter, double* stats);
+                      double* xseg, double* hist, int32_t* iter, double* stats,
+                      const uint8_t* drop, int32_t* held);
 
 #ifdef __cplusplus
 }
