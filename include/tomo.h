@@ -264,6 +264,8 @@ typedef struct {
     int km_k, km_iters, jpeg_quality;
     uint64_t seed;
     int mode;
+    int max_stale; /* >= 0: extra iterations a held message may age through losses
+                      (dadmm_step_lossy); deepens the message ring by as many planes */
 } dadmm_config;
 
 typedef struct dadmm* dadmm_t;
@@ -326,7 +328,10 @@ TOMO_API size_t dadmm_workspace_size(dadmm_t h);
  * stats: HOST [n_iters][S][DADMM_NSTAT] or NULL; when non-NULL the call
  * synchronizes the stream, fills it and checks the device status word:
  * TOMO_ERR_NUMERIC if a statistic is not finite (the state is still
- * advanced), TOMO_ERR_TIMEOUT if a bounded device wait gave up. */
+ * advanced), TOMO_ERR_TIMEOUT if a bounded device wait gave up.
+ * Right after dadmm_step_lossy calls that left some node holding an old
+ * message version, the first iteration still reads that version (the
+ * exchange then brings every node up to date); that call synchronizes once. */
 TOMO_API tomo_status dadmm_step(dadmm_t h, const dadmm_state* st, const float* sino, int n_iters,
                        void* workspace, size_t workspace_bytes, double* stats,
                        tomo_stream_t stream);
@@ -340,6 +345,23 @@ TOMO_API tomo_status dadmm_step(dadmm_t h, const dadmm_state* st, const float* s
  * (step or status read) zeroes it, so fresh memory needs no initialisation. */
 TOMO_API tomo_status dadmm_sync_status(dadmm_t h, void* workspace, size_t workspace_bytes,
                                        tomo_stream_t stream);
+
+/* dadmm_step with lost messages (a decentralized extension of Algorithm 4):
+ * drop is a HOST array [n_iters][M][M] (n_iters <= DADMM_MAX_LOSSY_ITERS);
+ * drop[i][s][m] != 0 means node m loses owner s's message in the exchange of
+ * the i-th iteration of this call and keeps the version it holds; otherwise
+ * it receives the newest version that has reached it over the relay. A
+ * node's own segment is never lost (drop[i][m][m] is ignored). The versions
+ * every node holds are tracked on the host, starting from the lossless ones
+ * whenever the iteration counter differs from where the previous lossy call
+ * ended. Requires a handle created with max_stale > 0; a mask that would make
+ * a held version older than the message ring (max_stale extra iterations) is
+ * refused with TOMO_ERR_INVALID_ARG before anything is launched. Reads the
+ * iteration counter (synchronizes the stream once); otherwise as dadmm_step. */
+#define DADMM_MAX_LOSSY_ITERS 256
+TOMO_API tomo_status dadmm_step_lossy(dadmm_t h, const dadmm_state* st, const float* sino, int n_iters,
+                                      const uint8_t* drop, void* workspace, size_t workspace_bytes,
+                                      double* stats, tomo_stream_t stream);
 
 /* Per-phase timing of the iterations. When enabled, dadmm_step records a
  * CUDA event (timing enabled) before and after every phase launch of an

@@ -38,7 +38,7 @@ class DadmmConfig(C.Structure):
         ("adj", C.c_void_p), ("edge_q", C.c_void_p), ("home_q", C.c_void_p), ("eta1", C.c_void_p),
         ("eta2", C.c_double), ("rho", C.c_double), ("E1", C.c_int), ("E2", C.c_int),
         ("km_k", C.c_int), ("km_iters", C.c_int), ("jpeg_quality", C.c_int),
-        ("seed", C.c_uint64), ("mode", C.c_int),
+        ("seed", C.c_uint64), ("mode", C.c_int), ("max_stale", C.c_int),
     ]
 
 
@@ -80,6 +80,8 @@ SIGNATURES = {
     "dadmm_step": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_int, C.c_void_p,
                              C.c_size_t, C.c_void_p, C.c_void_p]),
     "dadmm_home_view": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_void_p]),
+    "dadmm_step_lossy": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "tomo_lincomb": (C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tomo_dot": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tomo_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -330,6 +332,7 @@ class DADMM:
         cfg.jpeg_quality = int(prob["jpeg_quality"])
         cfg.seed = int(prob["seed"])
         cfg.mode = MODE_BATCHED if mode == "batched" else MODE_PLAIN
+        cfg.max_stale = int(prob.get("max_stale", 0))
         self.mode = mode
         self.cfg = cfg
         h = C.c_void_p()
@@ -363,14 +366,27 @@ class DADMM:
     def reset(self):
         _check(lib().dadmm_state_init(self.handle, C.byref(self._state), _stream()))
 
-    def step(self, sino, n_iters=1, stats=True):
+    def step(self, sino, n_iters=1, stats=True, drop=None):
         """Run n_iters iterations on sino [S, A, B] (CUDA float32). Returns the
-        statistics [n_iters, S, 5] (numpy) when stats=True (synchronizes)."""
+        statistics [n_iters, S, 5] (numpy) when stats=True (synchronizes).
+        drop: optional [n_iters, M, M] (or [M, M] for every iteration) array,
+        drop[i, s, m] != 0 when node m loses owner s's message in iteration i
+        (needs max_stale > 0 in the problem)"""
         _require_cuda(sino)
         st = np.empty((n_iters, self.S, NSTAT), np.float64) if stats else None
-        _check(lib().dadmm_step(self.handle, C.byref(self._state), _ptr(sino), int(n_iters),
-                                _ptr(self.workspace), self.ws_bytes,
-                                st.ctypes.data_as(C.c_void_p) if stats else None, _stream()))
+        sp = st.ctypes.data_as(C.c_void_p) if stats else None
+        if drop is None:
+            _check(lib().dadmm_step(self.handle, C.byref(self._state), _ptr(sino), int(n_iters),
+                                    _ptr(self.workspace), self.ws_bytes, sp, _stream()))
+        else:
+            d = np.asarray(drop, np.uint8)
+            if d.ndim == 2:
+                d = np.broadcast_to(d, (n_iters, self.M, self.M))
+            d = np.ascontiguousarray(d)
+            assert d.shape == (n_iters, self.M, self.M)
+            _check(lib().dadmm_step_lossy(self.handle, C.byref(self._state), _ptr(sino), int(n_iters),
+                                          d.ctypes.data_as(C.c_void_p), _ptr(self.workspace), self.ws_bytes, sp,
+                                          _stream()))
         return st
 
     def sync_status(self):

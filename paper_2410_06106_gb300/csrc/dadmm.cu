@@ -79,6 +79,15 @@ struct Dadmm {
     const void* ut_u = nullptr;
     const void* ut_ws = nullptr;
     bool ut_dirty = true;
+    // lost messages: versions held [node][segment] after iteration held_k (host), the
+    // table of the current lossy call, and whether the captured graph reads it
+    int max_stale = 0;
+    std::vector<int32_t> held;
+    int held_k = -1;
+    bool held_stale = false;  // some node held an old version after iteration held_k
+    std::vector<int32_t> held_tab;
+    bool lossy = false;
+    size_t off_held = 0;
     // TMA descriptors of u and of its transposed copy (rebuilt with the graph)
     CUtensorMap map_u{}, map_uT{};
     int has_maps = 0;
@@ -112,6 +121,8 @@ struct ElemParams {
     const int32_t* seg_of_row;
     const int8_t* lag;
     const int8_t* kind;
+    const int32_t* held;     // lossy steps: [iteration - *k_first][2][M][M] (null: lag rule)
+    const int32_t* k_first;
     const int32_t* need;
     unsigned* lo_key;
     unsigned* hi_key;
@@ -170,10 +181,12 @@ __global__ void __launch_bounds__(kElemThreads) xstep_kernel(const ElemParams p,
     }
 }
 
-__device__ __forceinline__ const float* view_row(const ElemParams& p, int slice, int m, int i, int k) {
+// node m's view of row i at time k (= the current iteration kcur, or kcur + 1):
+// the message version the relay rule gives, or, in lossy steps, the one held
+__device__ __forceinline__ const float* view_row(const ElemParams& p, int slice, int m, int i, int k, int kcur) {
     const int seg = p.seg_of_row[i];
     const int mi = m * p.M + seg;
-    const int j = k - p.lag[mi];
+    const int j = p.held ? p.held[((size_t)(kcur - *p.k_first) * 2 + (k - kcur)) * p.M * p.M + mi] : k - p.lag[mi];
     if (j < 1) return nullptr;
     const size_t n = (size_t)p.N * p.N;
     return p.hist + (((size_t)(j % p.D) * 3 + p.kind[mi]) * p.S + slice) * n + (size_t)i * p.N;
@@ -194,8 +207,8 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
         const size_t o = ((size_t)slice * p.M + node) * n + (size_t)i * N;
         const float* u = p.u + o;
         float* l = p.lam + o;
-        const float* x1 = view_row(p, slice, node, i, k + 1);
-        const float* x0 = node == 0 ? view_row(p, slice, node, i, k) : nullptr;
+        const float* x1 = view_row(p, slice, node, i, k + 1, k);
+        const float* x0 = node == 0 ? view_row(p, slice, node, i, k, k) : nullptr;
         float g = 0.f, c = 0.f, q = 0.f;
         for (int j = threadIdx.x; j < N; j += kElemThreads) {
             const float xv = x1 ? x1[j] : 0.f;
@@ -455,6 +468,7 @@ struct WsPtrs {
     unsigned* lo;
     unsigned* hi;
     long long* nnz;      // [S][M] entropy-coded JPEG message bytes
+    int32_t* held;       // lossy steps: k_first, then the held-version table
     int16_t* coefs;      // quantized blocks of the JPEG segments
     uint32_t* bits;      // their entropy-coding bit buffers
     double* dual;
@@ -472,6 +486,7 @@ static WsPtrs ws_ptrs(const Dadmm& h, void* ws) {
     w.lo = (unsigned*)(b + h.off_lo);
     w.hi = (unsigned*)(b + h.off_hi);
     w.nnz = (long long*)(b + h.off_nnz);
+    w.held = h.max_stale > 0 ? (int32_t*)(b + h.off_held) : nullptr;
     w.coefs = (int16_t*)(b + h.off_coefs);
     w.bits = (uint32_t*)(b + h.off_bits);
     w.dual = (double*)(b + h.off_dual);
@@ -491,6 +506,8 @@ static ElemParams elem_params(const Dadmm& h, const dadmm_state& st, const WsPtr
     p.seg_of_row = h.d_seg_of_row;
     p.lag = h.d_lag;
     p.kind = h.d_kind;
+    p.held = h.lossy ? w.held + 4 : nullptr;  // the first 16 bytes hold k_first
+    p.k_first = h.lossy ? w.held : nullptr;
     p.need = h.d_need;
     p.lo_key = w.lo;
     p.hi_key = w.hi;
@@ -551,6 +568,8 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     bp.view.hist = st.hist;
     bp.view.iter = st.iter;
     bp.view.lag = h.d_lag;
+    bp.view.held = h.lossy ? w.held + 4 : nullptr;
+    bp.view.k_first = h.lossy ? w.held : nullptr;
     bp.view.kind = h.d_kind;
     bp.view.seg_of_row = h.d_seg_of_row;
     bp.view.eta1 = h.d_eta1;
@@ -774,7 +793,11 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->A = A;
             h->S = c.S;
             h->M = M;
-            h->D = max_lag + 2;  // ring also keeps node 0's previous view for the change statistic
+            TOMO_REQUIRE(c.max_stale >= 0 && c.max_stale <= 64, "max_stale must be in [0, 64]");
+            h->max_stale = c.max_stale;
+            // the ring also keeps node 0's previous view for the change statistic, and
+            // max_stale older versions for nodes that lost messages
+            h->D = max_lag + 2 + c.max_stale;
             h->E1 = c.E1;
             h->E2 = c.E2;
             h->rho = c.rho;
@@ -925,6 +948,8 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->off_lo = take(sizeof(unsigned) * SMn);
             h->off_hi = take(sizeof(unsigned) * SMn);
             h->off_nnz = take(sizeof(long long) * SMn);
+            if (c.max_stale > 0)
+                h->off_held = take(sizeof(int32_t) * (4 + (size_t)DADMM_MAX_LOSSY_ITERS * 2 * M * M));
             h->off_coefs = take(sizeof(int16_t) * 64 * (size_t)std::max(jp_blocks, 1LL));
             h->off_bits = take(sizeof(uint32_t) * ((size_t)jp_blocks * kEntropyWordsPerBlock + jp.size() + 1));
             h->off_dual = take(sizeof(double) * 3 * SMn * kDualPerNode);
@@ -973,11 +998,16 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
         TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * (size_t)h.D * 3 * h.S * n, s));
         TOMO_CUDA(cudaMemsetAsync(st->iter, 0, sizeof(int32_t), s));
         h.ut_dirty = true;
+        h.held_k = -1;
     });
 }
 
 tomo_status dadmm_state_modified(dadmm_t hh) {
-    return guard([&] { as_dadmm(hh)->ut_dirty = true; });
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        h.ut_dirty = true;
+        h.held_k = -1;  // held versions restart from the lossless ones at the next lossy call
+    });
 }
 
 tomo_status dadmm_sync_status(dadmm_t hh, void* workspace, size_t workspace_bytes, tomo_stream_t stream) {
@@ -1007,12 +1037,56 @@ tomo_status dadmm_sync_status(dadmm_t hh, void* workspace, size_t workspace_byte
     return rc;
 }
 
-tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters, void* workspace,
-                       size_t workspace_bytes, double* stats, tomo_stream_t stream) {
+}  // extern "C"
+
+namespace tomo {
+
+// the held-version table of a lossy call: row i = (versions held at iteration k0+i, at k0+i+1);
+// refuses a mask under which a version read would have left the ring
+static void build_held_table(Dadmm& h, int k0, int n_iters, const uint8_t* drop) {
+    const int M = h.M, MM = M * M, D = h.D;
+    if ((int)h.held.size() != MM || h.held_k != k0) {  // the lossless versions at k0
+        h.held.assign(MM, 0);
+        for (int m = 0; m < M; ++m)
+            for (int sg = 0; sg < M; ++sg) h.held[m * M + sg] = std::max(0, k0 - (int)h.lag[m * M + sg]);
+    }
+    h.held_tab.assign((size_t)n_iters * 2 * MM, 0);
+    std::vector<int32_t> next(MM);
+    for (int i = 0; i < n_iters; ++i) {
+        const int k = k0 + i;
+        for (int m = 0; m < M; ++m)
+            for (int sg = 0; sg < M; ++sg) {
+                const int mi = m * M + sg;
+                const int newest = k + 1 - (int)h.lag[mi];
+                const bool lost = sg != m && drop[((size_t)i * M + sg) * M + m] != 0;
+                next[mi] = (!lost && newest >= 1) ? newest : h.held[mi];
+                const int v0 = h.held[mi], v1 = next[mi];
+                const bool ok = (v0 < 1 || v0 >= k + 1 - D) && (v1 < 1 || v1 >= k + 2 - D) &&
+                                (m != 0 || v0 < 1 || v0 >= k + 2 - D);
+                TOMO_REQUIRE(ok, "lost messages would make node " + std::to_string(m) + " read a version of segment " +
+                                     std::to_string(sg) + " older than the message ring (raise max_stale)");
+            }
+        std::memcpy(&h.held_tab[(size_t)i * 2 * MM], h.held.data(), sizeof(int32_t) * MM);
+        std::memcpy(&h.held_tab[((size_t)i * 2 + 1) * MM], next.data(), sizeof(int32_t) * MM);
+        h.held.swap(next);
+    }
+    h.held_k = k0 + n_iters;
+    h.held_stale = false;
+    for (int mi = 0; mi < MM; ++mi)
+        h.held_stale |= h.held[mi] != std::max(0, h.held_k - (int)h.lag[mi]);
+}
+
+static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters,
+                             const uint8_t* drop, void* workspace, size_t workspace_bytes, double* stats,
+                             tomo_stream_t stream) {
     tomo_status numeric = TOMO_OK;
     tomo_status rc = guard([&] {
         Dadmm& h = *as_dadmm(hh);
         check_device(*h.g);
+        if (drop) {
+            TOMO_REQUIRE(h.max_stale > 0, "lossy steps need a handle created with max_stale > 0");
+            TOMO_REQUIRE(n_iters <= DADMM_MAX_LOSSY_ITERS, "n_iters above DADMM_MAX_LOSSY_ITERS");
+        }
         TOMO_REQUIRE(st && st->u && st->lam && st->xseg && st->hist && st->iter, "state pointers must be non-NULL");
         TOMO_REQUIRE(sino != nullptr, "sino is NULL");
         TOMO_REQUIRE(n_iters >= 0, "n_iters must be >= 0");
@@ -1024,10 +1098,17 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
         cudaStream_t user = (cudaStream_t)stream;
         const WsPtrs w = ws_ptrs(h, workspace);
         int k0 = 0;
-        if (stats) {
+        if (stats || drop) {
             TOMO_CUDA(cudaMemcpyAsync(&k0, st->iter, sizeof(int), cudaMemcpyDeviceToHost, user));
             TOMO_CUDA(cudaStreamSynchronize(user));
         }
+        if (drop) {  // the versions held at every iteration of this call, and the first one's index
+            build_held_table(h, k0, n_iters, drop);
+            TOMO_CUDA(cudaMemcpyAsync(w.held, &k0, sizeof(int32_t), cudaMemcpyHostToDevice, user));
+            TOMO_CUDA(cudaMemcpyAsync(w.held + 4, h.held_tab.data(), sizeof(int32_t) * h.held_tab.size(),
+                                      cudaMemcpyHostToDevice, user));
+        }
+        h.lossy = drop != nullptr;
         if (stats || workspace != h.ws_status_init) {  // the status word covers this call (or starts here)
             TOMO_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), user));
             h.ws_status_init = workspace;
@@ -1050,7 +1131,7 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
         }
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
-                                                  w.resid};
+                                                  w.resid, (const void*)(uintptr_t)(h.lossy ? 1 : 0)};
             if (!h.gexec || key != h.gkey) {
                 if (h.gexec) {
                     TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
@@ -1103,6 +1184,43 @@ tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int
         return numeric;
     }
     return rc;
+}
+
+}  // namespace tomo
+
+extern "C" {
+
+tomo_status dadmm_step(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters, void* workspace,
+                       size_t workspace_bytes, double* stats, tomo_stream_t stream) {
+    // after lost messages some nodes still hold old versions at the next iteration: that
+    // one iteration reads them (a lossless exchange brings every node up to date)
+    tomo::Dadmm* h = hh ? tomo::as_dadmm(hh) : nullptr;
+    if (h && h->held_stale && n_iters > 0 && st && st->iter) {
+        int k0 = -1;
+        if (cudaMemcpyAsync(&k0, st->iter, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+            cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+            tomo::set_last_error("reading the iteration counter failed");
+            return TOMO_ERR_CUDA;
+        }
+        if (k0 == h->held_k) {
+            const std::vector<uint8_t> none((size_t)h->M * h->M, 0);
+            tomo_status rc = tomo::run_steps(hh, st, sino, 1, none.data(), workspace, workspace_bytes, stats, stream);
+            if (rc != TOMO_OK || n_iters == 1) return rc;
+            return tomo::run_steps(hh, st, sino, n_iters - 1, nullptr, workspace, workspace_bytes,
+                                   stats ? stats + (size_t)h->S * DADMM_NSTAT : nullptr, stream);
+        }
+        h->held_stale = false;  // the state moved on without this handle's lossy calls
+    }
+    return tomo::run_steps(hh, st, sino, n_iters, nullptr, workspace, workspace_bytes, stats, stream);
+}
+
+tomo_status dadmm_step_lossy(dadmm_t hh, const dadmm_state* st, const float* sino, int n_iters, const uint8_t* drop,
+                             void* workspace, size_t workspace_bytes, double* stats, tomo_stream_t stream) {
+    if (!drop) {
+        tomo::set_last_error("drop is NULL");
+        return TOMO_ERR_INVALID_ARG;
+    }
+    return tomo::run_steps(hh, st, sino, n_iters, drop, workspace, workspace_bytes, stats, stream);
 }
 
 tomo_status dadmm_set_profiling(dadmm_t hh, int enable) {

@@ -578,7 +578,11 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         cp_async_commit();
     }
     int kiter = 0;
-    if (EPI == EPI_USTEP) kiter = *p.view.iter;
+    const int32_t* held = nullptr;  // lossy steps: the versions each node holds at this iteration
+    if (EPI == EPI_USTEP) {
+        kiter = *p.view.iter;
+        if (p.view.held) held = p.view.held + (size_t)(kiter - *p.view.k_first) * 2 * p.view.M * p.view.M;
+    }
 
     float acc[4][4];
 #pragma unroll
@@ -686,7 +690,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 for (int ky = 0; ky < 4; ++ky) {
                     const int row = min(y0 + ty + 16 * ky, N - 1);
                     const int mi = cur.node * V.M + V.seg_of_row[row];
-                    const int jj = kiter - V.lag[mi];
+                    const int jj = held ? held[mi] : kiter - V.lag[mi];
                     xrow[ky] = jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +
                                              (size_t)row * N
                                        : nullptr;

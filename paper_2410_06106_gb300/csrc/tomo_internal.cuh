@@ -211,6 +211,8 @@ struct BpView {  // dADMM epilogue: where every node's view of x lives
     const float* hist;        // [D][3][S][N][N]
     const int32_t* iter;      // completed iterations k
     const int8_t* lag;        // [M][M] (node, segment) -> relay lag
+    const int32_t* held;      // lossy steps: [iteration - *k_first][2][M][M] versions held (null: lag rule)
+    const int32_t* k_first;   // iteration of the held table's first row
     const int8_t* kind;       // [M][M] (node, segment) -> quantizer plane
     const int32_t* seg_of_row;  // [N]
     const float* eta1;        // [M]
