@@ -45,6 +45,8 @@ def lib():
             "orc_huff_code": (None, [i32, i32, p, p]),
             "orc_zigzag": (None, [p]),
             "orc_relay_tables": (None, [i32, p, p, p]),
+            "orc_consensus_iterate": (i32, [i32, i32, i32, i32, i32, p, p, p, p, p, p, p,
+                                            d, p, i32, i32, i32, i32, u64, p, p, p, p, p, p]),
             "orc_dadmm_iterate": (i32, [i32, i32, i32, i32, i32, p, p, p, p, p, p, p, p,
                                         d, p, d, i32, i32, i32, i32, i32, u64, i32,
                                         p, p, p, p, p, p, p, p, p]),
@@ -314,3 +316,47 @@ class DADMM:
             r0, r1 = self.seg_row_ptr[m], self.seg_row_ptr[m + 1]
             out[:, r0:r1] = self.hist[slot, self.home_q[m], :, r0:r1]
         return out
+
+
+class Consensus:
+    """Oracle state of the neighbour-averaged consensus variant: u, lam and
+    every node's own x, all [S, M, N, N] float64; k completed iterations."""
+
+    def __init__(self, prob, eta1, S=None):
+        self.p = prob
+        g = prob["geometry"]
+        self.N, self.B, self.A = g["N"], g["B"], g["A"]
+        self.M = prob["M"]
+        self.S = prob["S"] if S is None else S
+        self.c, self.s = trig(_f64(g["theta"]))
+        self.node_ang_ptr = _i32(prob["node_ang_ptr"])
+        self.node_ang = _i32(prob["node_ang"])
+        self.adj = _i32(prob["adj"])
+        self.edge_q = _i32(prob["edge_q"])
+        self.home_q = _i32(prob["home_q"])
+        self.eta1 = _f64(eta1)
+        N, M, S = self.N, self.M, self.S
+        self.u = np.zeros((S, M, N, N))
+        self.lam = np.zeros((S, M, N, N))
+        self.x = np.zeros((S, M, N, N))
+        self.k = 0
+
+    def load_state(self, u, lam, x, k):
+        self.u, self.lam, self.x = _f64(u).copy(), _f64(lam).copy(), _f64(x).copy()
+        self.k = int(k)
+
+    def iterate(self, sino):
+        p = self.p
+        d = _f64(sino)
+        it = np.array([self.k], np.int32)
+        stats = np.empty((self.S, NSTAT), np.float64)
+        rc = lib().orc_consensus_iterate(
+            self.N, self.B, self.A, self.S, self.M, _ptr(self.c), _ptr(self.s),
+            _ptr(self.node_ang_ptr), _ptr(self.node_ang), _ptr(self.adj), _ptr(self.edge_q), _ptr(self.home_q),
+            float(p["rho"]), _ptr(self.eta1), int(p["E1"]), int(p["km_k"]), int(p["km_iters"]),
+            int(p["jpeg_quality"]), int(p["seed"]), _ptr(d), _ptr(self.u), _ptr(self.lam), _ptr(self.x),
+            _ptr(it), _ptr(stats))
+        if rc != 0:
+            raise ValueError("orc_consensus_iterate failed: %d" % rc)
+        self.k = int(it[0])
+        return stats

@@ -888,3 +888,130 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
     free(dist); free(first);
     return 0;
 }
+
+
+/* ---------------------------------------------------------------------
+ * Neighbour-averaged consensus: the decentralized analogue of the standard
+ * ADMM x-update (Eq. 9: x = mean over all nodes of u_m + lambda_m / rho).
+ * Every node keeps its own consensus image x_m and averages, over its closed
+ * neighbourhood (itself and its graph neighbours), the messages
+ * Q(u_j^{k+1} + lambda_j^k / rho) it receives in this iteration's exchange:
+ *   u_m^{k+1}  = Algorithm 2 with x_m^k (warm start from u_m^k)
+ *   v_j        = u_j^{k+1} + lambda_j^k / rho, quantized by the edge's
+ *                quantizer (home quantizer for the node's own term)
+ *   x_m^{k+1}  = (1 / |N[m]|) sum_{j in N[m]} Q_{j->m}(v_j)
+ *   lambda_m^{k+1} = lambda_m^k + rho (u_m^{k+1} - x_m^{k+1})
+ * On a complete graph without quantization this is Eq. 8-10 exactly.
+ * State: u, lam [S][M][N*N], x [S][M][N*N]; stats as orc_dadmm_iterate
+ * (chg2 / nrm2 of node 0's x; bytes = every message sent to a neighbour).
+ * ------------------------------------------------------------------- */
+int orc_consensus_iterate(int N, int B, int A, int S, int M,
+                          const double* c, const double* s,
+                          const int32_t* node_ang_ptr, const int32_t* node_ang,
+                          const int32_t* adj, const int32_t* edge_q, const int32_t* home_q,
+                          double rho, const double* eta1, int E1,
+                          int km_k, int km_iters, int jpeg_quality, uint64_t seed,
+                          const double* sino, double* u, double* lam, double* x,
+                          int32_t* iter, double* stats) {
+    const long n = (long)N * N;
+    if (N <= 0 || B <= 0 || M <= 0 || S <= 0 || km_k > 256) return -1;
+    const int k = *iter;
+    double* g = (double*)malloc(sizeof(double) * n);
+    double* r = (double*)malloc(sizeof(double) * (long)A * B);
+    double* msg = (double*)malloc(sizeof(double) * 3 * M * n); /* [kind][j][n] of one slice */
+    double* xn = (double*)malloc(sizeof(double) * n);
+    float* v32 = (float*)malloc(sizeof(float) * n);
+    float* deq32 = (float*)malloc(sizeof(float) * n);
+    uint8_t* codes = (uint8_t*)malloc((size_t)n);
+    int16_t* coefs = (int16_t*)malloc(sizeof(int16_t) * n);
+    float cent[256], lohi[2];
+    int bits = 0;
+    while ((1 << bits) < km_k) ++bits;
+
+    for (int sl = 0; sl < S; ++sl) {
+        double resid2 = 0.0, bytes = 0.0, gap2 = 0.0, chg2 = 0.0, nrm2 = 0.0;
+        const double* d_sl = sino + (long)sl * A * B;
+        /* Algorithm 2 on every node with its own x_m^k */
+        for (int m = 0; m < M; ++m) {
+            double* um = u + ((long)sl * M + m) * n;
+            const double* lm = lam + ((long)sl * M + m) * n;
+            const double* xm = x + ((long)sl * M + m) * n;
+            const int na = node_ang_ptr[m + 1] - node_ang_ptr[m];
+            const int32_t* ang = node_ang + node_ang_ptr[m];
+            for (int e = 0; e < E1; ++e) {
+                orc_project(N, B, c, s, na, ang, 1, um, r);
+                for (int q = 0; q < na; ++q)
+                    for (int b = 0; b < B; ++b) r[(long)q * B + b] -= d_sl[(long)ang[q] * B + b];
+                if (e == E1 - 1)
+                    for (long i = 0; i < (long)na * B; ++i) resid2 += r[i] * r[i];
+                orc_backproject(N, B, c, s, na, ang, 1, r, g);
+                for (long i = 0; i < n; ++i) {
+                    const double delta = g[i] + rho * (um[i] - (xm[i] - lm[i] / rho));
+                    um[i] -= eta1[m] * delta;
+                }
+            }
+        }
+        /* every node's message v_j in the quantizers it is sent with */
+        for (int j = 0; j < M; ++j) {
+            const double* uj = u + ((long)sl * M + j) * n;
+            const double* lj = lam + ((long)sl * M + j) * n;
+            double* v = msg + (0L * M + j) * n;
+            for (long i = 0; i < n; ++i) v[i] = uj[i] + lj[i] / rho;
+            int need[3] = {0, 0, 0};
+            need[home_q[j]] = 1;
+            for (int m = 0; m < M; ++m)
+                if (m != j && adj[j * M + m]) need[edge_q[j * M + m]] = 1;
+            for (long i = 0; i < n; ++i) v32[i] = (float)v[i];
+            double kind_bytes[3] = {4.0 * n, 0.0, 0.0};
+            if (need[ORC_Q_KMEANS]) {
+                orc_kmeans(v32, n, km_k, km_iters, orc_kmeans_key(seed, sl, j, k + 1), codes, cent, deq32, NULL);
+                for (long i = 0; i < n; ++i) msg[(1L * M + j) * n + i] = deq32[i];
+                kind_bytes[1] = bits * (double)n / 8.0 + 4.0 * km_k;
+            }
+            if (need[ORC_Q_JPEG]) {
+                orc_jpeg(v32, N, N, jpeg_quality, coefs, lohi, deq32);
+                for (long i = 0; i < n; ++i) msg[(2L * M + j) * n + i] = deq32[i];
+                const int64_t eb = (lohi[1] > lohi[0]) ? orc_jpeg_entropy(coefs, n / 64, NULL) : 0;
+                kind_bytes[2] = (double)eb + 8.0;
+            }
+            for (int m = 0; m < M; ++m)
+                if (m != j && adj[j * M + m]) bytes += kind_bytes[edge_q[j * M + m]];
+        }
+        /* neighbourhood averages and dual update */
+        for (int m = 0; m < M; ++m) {
+            double* xm = x + ((long)sl * M + m) * n;
+            const double* um = u + ((long)sl * M + m) * n;
+            double* lm = lam + ((long)sl * M + m) * n;
+            int cnt = 1;
+            const double* own = msg + ((long)home_q[m] * M + m) * n;
+            for (long i = 0; i < n; ++i) xn[i] = own[i];
+            for (int j = 0; j < M; ++j)
+                if (j != m && adj[j * M + m]) {
+                    const double* mj = msg + ((long)edge_q[j * M + m] * M + j) * n;
+                    for (long i = 0; i < n; ++i) xn[i] += mj[i];
+                    ++cnt;
+                }
+            for (long i = 0; i < n; ++i) xn[i] /= cnt;
+            if (m == 0)
+                for (long i = 0; i < n; ++i) {
+                    chg2 += (xn[i] - xm[i]) * (xn[i] - xm[i]);
+                    nrm2 += xm[i] * xm[i];
+                }
+            for (long i = 0; i < n; ++i) {
+                xm[i] = xn[i];
+                const double pr = um[i] - xm[i];
+                gap2 += pr * pr;
+                lm[i] += rho * pr;
+            }
+        }
+        double* st = stats + (long)sl * ORC_NSTAT;
+        st[0] = gap2;
+        st[1] = chg2;
+        st[2] = nrm2;
+        st[3] = resid2;
+        st[4] = bytes;
+    }
+    *iter = k + 1;
+    free(g); free(r); free(msg); free(xn); free(v32); free(deq32); free(codes); free(coefs);
+    return 0;
+}

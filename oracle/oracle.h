@@ -139,6 +139,18 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       double* xseg, double* hist, int32_t* iter, double* stats,
                       const uint8_t* drop, int32_t* held);
 
+/* Neighbour-averaged consensus (the decentralized analogue of Eq. 9; see
+ * oracle.c): x [S][M][N*N] is every node's own consensus image; messages are
+ * full images u_j + lambda_j / rho quantized per edge. */
+int orc_consensus_iterate(int N, int B, int A, int S, int M,
+                          const double* c, const double* s,
+                          const int32_t* node_ang_ptr, const int32_t* node_ang,
+                          const int32_t* adj, const int32_t* edge_q, const int32_t* home_q,
+                          double rho, const double* eta1, int E1,
+                          int km_k, int km_iters, int jpeg_quality, uint64_t seed,
+                          const double* sino, double* u, double* lam, double* x,
+                          int32_t* iter, double* stats);
+
 #ifdef __cplusplus
 }
 #endif
