@@ -266,7 +266,21 @@ typedef struct {
     int mode;
     int max_stale; /* >= 0: extra iterations a held message may age through losses
                       (dadmm_step_lossy); deepens the message ring by as many planes */
+    int variant;   /* DADMM_VARIANT_SEGMENTS (Algorithm 4) or DADMM_VARIANT_CONSENSUS */
 } dadmm_config;
+
+/* Algorithm 4: every node owns a segment of x and the segments travel over the
+ * graph (the paper's decentralized ADMM). */
+#define DADMM_VARIANT_SEGMENTS 0
+/* Neighbour-averaged consensus, the decentralized analogue of the standard
+ * ADMM x-update (Eq. 9): every node keeps its own x_m and sets it to the mean,
+ * over its closed neighbourhood, of the messages Q(u_j + lambda_j / rho)
+ * (full images; the edge's quantizer, the home quantizer for its own term);
+ * messages travel one hop per iteration. The state's xseg is then x
+ * [S][M][N][N] and hist the message planes [3][S][M][N][N]; seg_row_ptr,
+ * eta2, E2 and max_stale are not used. On a complete graph without
+ * quantization this is Eq. 8-10. */
+#define DADMM_VARIANT_CONSENSUS 1
 
 typedef struct dadmm* dadmm_t;
 

@@ -38,7 +38,7 @@ class DadmmConfig(C.Structure):
         ("adj", C.c_void_p), ("edge_q", C.c_void_p), ("home_q", C.c_void_p), ("eta1", C.c_void_p),
         ("eta2", C.c_double), ("rho", C.c_double), ("E1", C.c_int), ("E2", C.c_int),
         ("km_k", C.c_int), ("km_iters", C.c_int), ("jpeg_quality", C.c_int),
-        ("seed", C.c_uint64), ("mode", C.c_int), ("max_stale", C.c_int),
+        ("seed", C.c_uint64), ("mode", C.c_int), ("max_stale", C.c_int), ("variant", C.c_int),
     ]
 
 
@@ -333,6 +333,10 @@ class DADMM:
         cfg.seed = int(prob["seed"])
         cfg.mode = MODE_BATCHED if mode == "batched" else MODE_PLAIN
         cfg.max_stale = int(prob.get("max_stale", 0))
+        self.variant = prob.get("variant", "segments")
+        if self.variant not in ("segments", "consensus"):
+            raise TomoError(-1, "variant must be 'segments' or 'consensus'")
+        cfg.variant = 1 if self.variant == "consensus" else 0
         self.mode = mode
         self.cfg = cfg
         h = C.c_void_p()
@@ -343,8 +347,12 @@ class DADMM:
         n = self.N * self.N
         self.u = torch.zeros(self.S, self.M, self.N, self.N, device=dev)
         self.lam = torch.zeros(self.S, self.M, self.N, self.N, device=dev)
-        self.xseg = torch.zeros(self.S, self.N, self.N, device=dev)
-        self.hist = torch.zeros(self.D, 3, self.S, self.N, self.N, device=dev)
+        if self.variant == "consensus":  # every node's x, and the message planes of one exchange
+            self.xseg = torch.zeros(self.S, self.M, self.N, self.N, device=dev)
+            self.hist = torch.zeros(3, self.S, self.M, self.N, self.N, device=dev)
+        else:
+            self.xseg = torch.zeros(self.S, self.N, self.N, device=dev)
+            self.hist = torch.zeros(self.D, 3, self.S, self.N, self.N, device=dev)
         self.iter = torch.zeros(1, dtype=torch.int32, device=dev)
         self.ws_bytes = lib().dadmm_workspace_size(h)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)

@@ -152,12 +152,10 @@ __global__ void __launch_bounds__(kKmThreads) kmeans_dadmm_kernel(const DadmmCod
                                                                   int task_begin) {
     const SegTask T = p.tasks[task_begin + blockIdx.x];
     const int kk = *p.iter;  // completed iterations: the messages are x^{k+1}
-    const size_t n = (size_t)p.N * p.N;
-    const size_t off = (size_t)T.slice * n + (size_t)T.r0 * p.N;
     const long long len = (long long)(T.r1 - T.r0) * p.N;
     const int slot = (kk + 1) % p.D;
-    float* deq = p.hist + ((size_t)slot * 3 + DADMM_Q_KMEANS) * p.S * n + off;
-    kmeans_block<KMAX>(p.xseg + off, len, k, iters, kmeans_key(p.seed, T.slice, T.owner, kk + 1),
+    float* deq = p.hist + (size_t)slot * p.slot_stride + (size_t)DADMM_Q_KMEANS * p.plane_stride + T.dst_off;
+    kmeans_block<KMAX>(p.xseg + T.src_off, len, k, iters, kmeans_key(p.seed, T.slice, T.owner, kk + 1),
                        nullptr, nullptr, deq, nullptr);
 }
 
@@ -509,16 +507,15 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_dadmm_kernel(const DadmmCod
     const int blk = blockIdx.x * kJpegThreads + threadIdx.x;
     if (blk < ((T.r1 - T.r0) / 8) * bpr) {
         const int kk = *p.iter;
-        const size_t n = (size_t)N * N;
         const int bi = blk / bpr, bj = blk - bi * bpr;
-        const size_t o = (size_t)T.slice * n + (size_t)(T.r0 + bi * 8) * N + (size_t)bj * 8;
+        const size_t o = (size_t)(bi * 8) * N + (size_t)bj * 8;  // within the segment
         const int slot = (kk + 1) % p.D;
-        float* dst = p.hist + ((size_t)slot * 3 + DADMM_Q_JPEG) * p.S * n + o;
+        float* dst = p.hist + (size_t)slot * p.slot_stride + (size_t)DADMM_Q_JPEG * p.plane_stride + T.dst_off + o;
         const float lo = key_float(p.lo_key[T.slice * p.M + T.owner]);
         const float hi = key_float(p.hi_key[T.slice * p.M + T.owner]);
         int16_t* cf = p.coefs + ((size_t)T.blk0 + blk) * 64;
         if (hi > lo) {
-            jpeg_block(p.xseg + o, dst, N, lo, hi, qt, cf, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
+            jpeg_block(p.xseg + T.src_off + o, dst, N, lo, hi, qt, cf, &s_smp[0][threadIdx.x], &s_q[0][threadIdx.x]);
         } else {
             jpeg_const_block(dst, N, lo);
             for (int e = 0; e < 64; ++e) cf[e] = 0;

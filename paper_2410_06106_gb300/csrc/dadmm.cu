@@ -88,6 +88,10 @@ struct Dadmm {
     std::vector<int32_t> held_tab;
     bool lossy = false;
     size_t off_held = 0;
+    // neighbour-averaged consensus variant: closed neighbourhoods (sender | quantizer << 16)
+    int variant = 0;
+    int32_t* d_nb_ptr = nullptr;
+    int32_t* d_nb = nullptr;
     // TMA descriptors of u and of its transposed copy (rebuilt with the graph)
     CUtensorMap map_u{}, map_uT{};
     int has_maps = 0;
@@ -364,6 +368,134 @@ __global__ void home_view_kernel(const float* hist, const int32_t* iter, const i
 }
 
 // ------------------------------------------------------------------
+// neighbour-averaged consensus variant (the decentralized analogue of the
+// standard ADMM x-update, Eq. 9): every node keeps its own x_m [S][M][N][N]
+// (in the state's x array) and averages the full-image messages of its closed
+// neighbourhood; the message planes are [3][S][M][N][N] (in the history array)
+// ------------------------------------------------------------------
+struct ConsParams {
+    ElemParams e;
+    float* x;              // [S][M][N][N] every node's consensus image
+    float* msg;            // [3][S][M][N][N] dequantized messages (plane 0: identity)
+    const int32_t* nb_ptr; // [M+1] closed neighbourhood of each node
+    const int32_t* nb;     // sender j | quantizer << 16: the node itself first, then its neighbours
+};
+
+// v_j = u_j + lambda_j / rho: node j's message before quantization (identity
+// plane and codec source), and its min / max for the JPEG sample map
+__global__ void __launch_bounds__(kElemThreads) cons_message_kernel(const ConsParams c, int row_begin, int row_count) {
+    __shared__ float s_lo[kElemThreads / 32], s_hi[kElemThreads / 32];
+    const ElemParams& p = c.e;
+    const int N = p.N;
+    for (int rr = blockIdx.x; rr < row_count; rr += gridDim.x) {
+        const int R = row_begin + rr;  // (slice * M + j) * N + i
+        const int img = R / N;         // slice * M + j
+        const size_t o = (size_t)R * N;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int j = threadIdx.x; j < N; j += kElemThreads) {
+            const float v = fmaf(p.lam[o + j], p.inv_rho, p.u[o + j]);
+            c.msg[o + j] = v;
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+        for (int q = 16; q > 0; q >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, q));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, q));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_lo[threadIdx.x >> 5] = lo;
+            s_hi[threadIdx.x >> 5] = hi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kElemThreads / 32; ++w) {
+                lo = fminf(lo, s_lo[w]);
+                hi = fmaxf(hi, s_hi[w]);
+            }
+            atomicMin(p.lo_key + img, float_key(lo));
+            atomicMax(p.hi_key + img, float_key(hi));
+        }
+        __syncthreads();
+    }
+}
+
+// x_m^{k+1} = mean over the closed neighbourhood of the received messages;
+// lambda_m += rho (u_m - x_m^{k+1}); FP64 partial norms as dual_kernel (the
+// change and norm statistics of node 0's x)
+__global__ void __launch_bounds__(kElemThreads) cons_dual_kernel(const ConsParams c, int node_begin, int slice_begin) {
+    __shared__ double s_red[3][kElemThreads / 32];
+    const ElemParams& p = c.e;
+    const int N = p.N, M = p.M;
+    const size_t n = (size_t)N * N, plane = (size_t)p.S * M * n;
+    const int slice = slice_begin + blockIdx.y;
+    const int node = node_begin + blockIdx.x / kDualPerNode;
+    const int part = blockIdx.x % kDualPerNode;
+    const int e0 = c.nb_ptr[node], e1 = c.nb_ptr[node + 1];
+    const float inv_cnt = 1.0f / (float)(e1 - e0);
+    double gap = 0.0, chg = 0.0, nrm = 0.0;
+    for (int i = part; i < N; i += kDualPerNode) {
+        const size_t o = ((size_t)slice * M + node) * n + (size_t)i * N;
+        float g = 0.f, ch = 0.f, q = 0.f;
+        for (int j = threadIdx.x; j < N; j += kElemThreads) {
+            float acc = 0.f;
+            for (int e = e0; e < e1; ++e) {
+                const int src = c.nb[e] & 0xFFFF, kd = c.nb[e] >> 16;
+                acc += c.msg[(size_t)kd * plane + ((size_t)slice * M + src) * n + (size_t)i * N + j];
+            }
+            const float xn = acc * inv_cnt;
+            if (node == 0) {
+                const float xo = c.x[o + j];
+                ch = fmaf(xn - xo, xn - xo, ch);
+                q = fmaf(xo, xo, q);
+            }
+            c.x[o + j] = xn;
+            const float pr = p.u[o + j] - xn;
+            g = fmaf(pr, pr, g);
+            p.lam[o + j] = fmaf(p.rho, pr, p.lam[o + j]);
+        }
+        gap += g;
+        chg += ch;
+        nrm += q;
+    }
+    for (int q = 16; q > 0; q >>= 1) {
+        gap += __shfl_xor_sync(0xffffffffu, gap, q);
+        chg += __shfl_xor_sync(0xffffffffu, chg, q);
+        nrm += __shfl_xor_sync(0xffffffffu, nrm, q);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_red[0][w] = gap;
+        s_red[1][w] = chg;
+        s_red[2][w] = nrm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int v = 0; v < kElemThreads / 32; ++v) {
+            a += s_red[0][v];
+            b += s_red[1][v];
+            cc += s_red[2][v];
+        }
+        double* d = p.dual_part + (((size_t)slice * M + node) * kDualPerNode + part) * 3;
+        d[0] = a;
+        d[1] = b;
+        d[2] = cc;
+    }
+}
+
+// the consensus reconstruction: the mean of the nodes' x
+__global__ void cons_view_kernel(const float* x, float* out, int N, int S, int M) {
+    const size_t n = (size_t)N * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)S * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t slice = e / n, o = e - slice * n;
+        float acc = 0.f;
+        for (int m = 0; m < M; ++m) acc += x[(slice * M + m) * n + o];
+        out[e] = acc / (float)M;
+    }
+}
+
+// ------------------------------------------------------------------
 // elementwise building blocks (linear combinations, FP64 dots)
 // ------------------------------------------------------------------
 struct LinComb {
@@ -455,7 +587,8 @@ static void free_dadmm(Dadmm* h) {
     if (h->own) cudaStreamDestroy(h->own);
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
     void* ptrs[] = {h->d_angs, h->d_bk, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
-                    h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_mx, h->d_km, h->d_jp};
+                    h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_mx, h->d_km, h->d_jp,
+                    h->d_nb_ptr, h->d_nb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -576,6 +709,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     bp.view.u = st.u;
     bp.view.uT = h.has_maps ? w.uT : nullptr;
     bp.view.lam = st.lam;
+    bp.view.xnode = h.variant == DADMM_VARIANT_CONSENSUS ? st.xseg : nullptr;
     bp.view.rho = (float)h.rho;
     bp.view.D = h.D;
     bp.view.S = h.S;
@@ -626,7 +760,58 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     cp.bits = w.bits;
     cp.jbytes = w.nnz;
     cp.M = h.M;
-    if (batched) {
+    const size_t nn = (size_t)h.N * h.N;
+    if (h.variant == DADMM_VARIANT_CONSENSUS) {
+        // messages: full images of every node, one exchange (no ring)
+        ConsParams cs{};
+        cs.e = ep;
+        cs.x = st.xseg;
+        cs.msg = st.hist;
+        cs.nb_ptr = h.d_nb_ptr;
+        cs.nb = h.d_nb;
+        cp.xseg = st.hist;  // the codecs read the identity plane
+        cp.plane_stride = (size_t)h.S * h.M * nn;
+        cp.slot_stride = 0;
+        const int rows = h.S * h.M * h.N;
+        if (batched) {
+            mark();
+            cons_message_kernel<<<std::min(rows, 152 * 8), kElemThreads, 0, s>>>(cs, 0, rows);
+            TOMO_CUDA(cudaGetLastError());
+            mark();
+            cp.tasks = h.d_km;
+            launch_kmeans_dadmm(cp, h.km_k, h.km_iters, 0, h.n_km, s);
+            mark();
+            cp.tasks = h.d_jp;
+            launch_jpeg_dadmm(cp, h.jpeg_q, h.max_jp_rows, 0, h.n_jp, s);
+            launch_jpeg_entropy_dadmm(cp, 0, h.n_jp, s);
+            mark();
+            cons_dual_kernel<<<dim3(h.M * kDualPerNode, h.S), kElemThreads, 0, s>>>(cs, 0, 0);
+            TOMO_CUDA(cudaGetLastError());
+        } else {
+            mark();
+            for (int img = 0; img < h.S * h.M; ++img) {
+                cons_message_kernel<<<h.N, kElemThreads, 0, s>>>(cs, img * h.N, h.N);
+                TOMO_CUDA(cudaGetLastError());
+            }
+            mark();
+            cp.tasks = h.d_km;
+            for (int t = 0; t < h.n_km; ++t) launch_kmeans_dadmm(cp, h.km_k, h.km_iters, t, 1, s);
+            mark();
+            cp.tasks = h.d_jp;
+            for (int t = 0; t < h.n_jp; ++t) {
+                launch_jpeg_dadmm(cp, h.jpeg_q, h.N, t, 1, s);
+                launch_jpeg_entropy_dadmm(cp, t, 1, s);
+            }
+            mark();
+            for (int sl = 0; sl < h.S; ++sl)
+                for (int m = 0; m < h.M; ++m) {
+                    cons_dual_kernel<<<dim3(kDualPerNode, 1), kElemThreads, 0, s>>>(cs, m, sl);
+                    TOMO_CUDA(cudaGetLastError());
+                }
+        }
+    } else if (batched) {
+        cp.plane_stride = (size_t)h.S * nn;
+        cp.slot_stride = 3 * (size_t)h.S * nn;
         const int rows = h.S * h.N;
         mark();
         xstep_kernel<<<std::min(rows, 152 * 8), kElemThreads, 0, s>>>(ep, 0, rows);
@@ -642,6 +827,8 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
         dual_kernel<<<dim3(h.M * kDualPerNode, h.S), kElemThreads, 0, s>>>(ep, 0, 0);
         TOMO_CUDA(cudaGetLastError());
     } else {
+        cp.plane_stride = (size_t)h.S * nn;
+        cp.slot_stride = 3 * (size_t)h.S * nn;
         mark();
         for (int sl = 0; sl < h.S; ++sl)
             for (int m = 0; m < h.M; ++m) {
@@ -692,6 +879,17 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     finalize_kernel<<<1, 256, 0, s>>>(fp);
     TOMO_CUDA(cudaGetLastError());
     mark();  // end of the last phase
+}
+
+// values of the state's x and history arrays (segment variant: x~ [S][N][N] and the
+// message ring [D][3][S][N][N]; consensus: x [S][M][N][N] and messages [3][S][M][N][N])
+static size_t x_values(const Dadmm& h) {
+    const size_t n = (size_t)h.N * h.N;
+    return h.variant == DADMM_VARIANT_CONSENSUS ? (size_t)h.S * h.M * n : (size_t)h.S * n;
+}
+static size_t hist_values(const Dadmm& h) {
+    const size_t n = (size_t)h.N * h.N;
+    return h.variant == DADMM_VARIANT_CONSENSUS ? 3 * (size_t)h.S * h.M * n : (size_t)h.D * 3 * h.S * n;
 }
 
 // device status word of a dADMM workspace: bit 0 projector extent (internal
@@ -756,6 +954,9 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
         TOMO_REQUIRE(c.E1 >= 0 && c.E1 <= 1000 && c.E2 >= 0 && c.E2 <= 100000, "E1/E2 out of range");
         TOMO_REQUIRE(c.rho > 0.0 && std::isfinite(c.rho), "rho must be positive");
         TOMO_REQUIRE(c.mode == DADMM_MODE_BATCHED || c.mode == DADMM_MODE_PLAIN, "unknown mode");
+        TOMO_REQUIRE(c.variant == DADMM_VARIANT_SEGMENTS || c.variant == DADMM_VARIANT_CONSENSUS, "unknown variant");
+        const bool cons = c.variant == DADMM_VARIANT_CONSENSUS;
+        TOMO_REQUIRE(!cons || c.max_stale == 0, "lost messages are a segment-variant feature");
         const int M = c.M, N = c.N, A = c.n_angles;
         // angle partition
         TOMO_REQUIRE(c.node_ang_ptr[0] == 0 && c.node_ang_ptr[M] == A, "node_ang_ptr must span all angles");
@@ -796,8 +997,9 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             TOMO_REQUIRE(c.max_stale >= 0 && c.max_stale <= 64, "max_stale must be in [0, 64]");
             h->max_stale = c.max_stale;
             // the ring also keeps node 0's previous view for the change statistic, and
-            // max_stale older versions for nodes that lost messages
-            h->D = max_lag + 2 + c.max_stale;
+            // max_stale older versions for nodes that lost messages (consensus: one exchange)
+            h->D = cons ? 1 : max_lag + 2 + c.max_stale;
+            h->variant = c.variant;
             h->E1 = c.E1;
             h->E2 = c.E2;
             h->rho = c.rho;
@@ -834,12 +1036,31 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                     }
                     h->kind[(size_t)m * M + s] = (int8_t)kd;
                 }
+            if (cons) {  // one hop: node j sends to its neighbours, each edge with its quantizer
+                std::fill(h->recv_cnt.begin(), h->recv_cnt.end(), 0);
+                std::vector<int32_t> nb_ptr(M + 1, 0), nb;
+                for (int m = 0; m < M; ++m) h->need[m] = 1 << h->home_q[m];
+                for (int m = 0; m < M; ++m) {
+                    nb.push_back(m | (h->home_q[m] << 16));
+                    for (int j = 0; j < M; ++j)
+                        if (j != m && adj[(size_t)j * M + m]) {
+                            const int kd = c.edge_q[(size_t)j * M + m];
+                            TOMO_REQUIRE(kd >= 0 && kd <= 2, "edge_q must be a DADMM_Q_* value on every edge");
+                            nb.push_back(j | (kd << 16));
+                            h->recv_cnt[(size_t)j * 3 + kd] += 1;
+                            h->need[j] |= 1 << kd;
+                        }
+                    nb_ptr[m + 1] = (int32_t)nb.size();
+                }
+                h->d_nb_ptr = device_upload(nb_ptr);
+                h->d_nb = device_upload(nb);
+            }
             bool any_km = false, any_jp = false;
             for (int m = 0; m < M; ++m) {
                 any_km |= (h->need[m] >> 1) & 1;
                 any_jp |= (h->need[m] >> 2) & 1;
                 if ((h->need[m] >> 2) & 1)
-                    TOMO_REQUIRE((h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]) % 8 == 0 && N % 8 == 0,
+                    TOMO_REQUIRE((cons || (h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]) % 8 == 0) && N % 8 == 0,
                                  "JPEG segments need row counts and N that are multiples of 8");
             }
             if (any_km) TOMO_REQUIRE(c.km_k >= 1 && c.km_k <= kKmMaxK && c.km_iters >= 0, "bad K-means settings");
@@ -894,8 +1115,8 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->d_lag = device_upload(h->lag);
             h->d_kind = device_upload(h->kind);
             h->d_seg_of_row = device_upload(seg_of_row);
-            std::vector<int32_t> need2(h->need);
-            for (int m = 0; m < M; ++m) need2.push_back(h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]);
+            std::vector<int32_t> need2(h->need);  // + the rows of every message (consensus: whole images)
+            for (int m = 0; m < M; ++m) need2.push_back(cons ? N : h->seg_row_ptr[m + 1] - h->seg_row_ptr[m]);
             h->d_need = device_upload(need2);
             h->d_recv = device_upload(h->recv_cnt);
             h->d_home = device_upload(h->home_q);
@@ -912,7 +1133,14 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->jp_index.assign((size_t)c.S * M, -1);
             for (int sl = 0; sl < c.S; ++sl)
                 for (int m = 0; m < M; ++m) {
-                    SegTask t{sl, m, h->seg_row_ptr[m], h->seg_row_ptr[m + 1], 0, 0, 0};
+                    SegTask t{sl, m, h->seg_row_ptr[m], h->seg_row_ptr[m + 1], 0, 0, 0, 0, 0};
+                    if (cons) {  // node m's whole message image
+                        t.r0 = 0;
+                        t.r1 = N;
+                        t.src_off = t.dst_off = ((long long)sl * M + m) * N * N;
+                    } else {
+                        t.src_off = t.dst_off = (long long)sl * N * N + (long long)t.r0 * N;
+                    }
                     if ((h->need[m] >> 1) & 1) {
                         h->km_index[(size_t)sl * M + m] = (int)km.size();
                         km.push_back(t);
@@ -980,7 +1208,7 @@ size_t dadmm_state_size(dadmm_t hh) {
     if (!hh) return 0;
     const Dadmm& h = *reinterpret_cast<Dadmm*>(hh);
     const size_t n = (size_t)h.N * h.N;
-    return sizeof(float) * (2 * (size_t)h.S * h.M * n + (size_t)h.S * n + (size_t)h.D * 3 * h.S * n) + sizeof(int32_t);
+    return sizeof(float) * (2 * (size_t)h.S * h.M * n + x_values(h) + hist_values(h)) + sizeof(int32_t);
 }
 
 size_t dadmm_workspace_size(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->ws_bytes : 0; }
@@ -994,8 +1222,8 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
         cudaStream_t s = (cudaStream_t)stream;
         TOMO_CUDA(cudaMemsetAsync(st->u, 0, sizeof(float) * h.S * h.M * n, s));
         TOMO_CUDA(cudaMemsetAsync(st->lam, 0, sizeof(float) * h.S * h.M * n, s));
-        TOMO_CUDA(cudaMemsetAsync(st->xseg, 0, sizeof(float) * h.S * n, s));
-        TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * (size_t)h.D * 3 * h.S * n, s));
+        TOMO_CUDA(cudaMemsetAsync(st->xseg, 0, sizeof(float) * x_values(h), s));
+        TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * hist_values(h), s));
         TOMO_CUDA(cudaMemsetAsync(st->iter, 0, sizeof(int32_t), s));
         h.ut_dirty = true;
         h.held_k = -1;
@@ -1257,8 +1485,11 @@ tomo_status dadmm_home_view(dadmm_t hh, const dadmm_state* st, float* out, tomo_
         Dadmm& h = *as_dadmm(hh);
         check_device(*h.g);
         TOMO_REQUIRE(st && st->hist && st->iter && out, "state and out must be non-NULL");
-        home_view_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(st->hist, st->iter, h.d_seg_of_row, h.d_home,
-                                                                  out, h.N, h.S, h.D);
+        if (h.variant == DADMM_VARIANT_CONSENSUS)
+            cons_view_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(st->xseg, out, h.N, h.S, h.M);
+        else
+            home_view_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(st->hist, st->iter, h.d_seg_of_row, h.d_home,
+                                                                      out, h.N, h.S, h.D);
         TOMO_CUDA(cudaGetLastError());
     });
 }

@@ -689,6 +689,10 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
 #pragma unroll
                 for (int ky = 0; ky < 4; ++ky) {
                     const int row = min(y0 + ty + 16 * ky, N - 1);
+                    if (V.xnode) {  // consensus variant: the node's own x
+                        xrow[ky] = V.xnode + (size_t)cur.img * n + (size_t)row * N;
+                        continue;
+                    }
                     const int mi = cur.node * V.M + V.seg_of_row[row];
                     const int jj = held ? held[mi] : kiter - V.lag[mi];
                     xrow[ky] = jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +

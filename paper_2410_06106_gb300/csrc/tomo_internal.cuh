@@ -218,6 +218,7 @@ struct BpView {  // dADMM epilogue: where every node's view of x lives
     const float* eta1;        // [M]
     float* u;                 // [S][M][N][N]
     float* uT;                // [S][M][N][N] transposed copy kept in step with u (may be null)
+    const float* xnode;       // consensus variant: every node's own x [S][M][N][N] (null: views)
     const float* lam;         // [S][M][N][N]
     float rho;
     int D, S, M;
@@ -278,11 +279,14 @@ struct SegTask {
     int blk0;          // JPEG: first of the segment's 8x8 blocks in the coefficient buffer
     int pad;
     long long word0;   // JPEG: first word of the segment's entropy-coding bit buffer
+    long long src_off; // first value of the segment in the codec's source array
+    long long dst_off; // first value of its message within a quantizer plane
 };
 
 struct DadmmCodec {
-    const float* xseg;    // [S][N][N]
-    float* hist;          // [D][3][S][N][N]
+    const float* xseg;    // the source values (segments: x~ [S][N][N]; consensus: v [S][M][N][N])
+    float* hist;          // message planes: slot * slot_stride + kind * plane_stride + dst_off
+    size_t plane_stride, slot_stride;
     const int32_t* iter;  // completed iterations k (messages belong to k+1)
     const SegTask* tasks;
     int n_tasks;
