@@ -287,8 +287,8 @@ typedef struct dadmm* dadmm_t;
 /* Create a solver for geometry g (which must outlive it). Builds the relay
  * tables (hop distance and first edge of the lowest-id shortest path from
  * every owner to every node), the persistent-kernel work lists and the
- * autotuned launch shapes. Allocates only small device tables owned by the
- * handle. */
+ * launch shapes (persistent grids sized by the occupancy API). Allocates only
+ * small device tables owned by the handle. */
 TOMO_API tomo_status dadmm_create(tomo_geometry_t g, const dadmm_config* cfg, dadmm_t* out);
 TOMO_API tomo_status dadmm_destroy(dadmm_t h);
 
