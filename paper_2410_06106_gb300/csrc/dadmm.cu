@@ -214,15 +214,52 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
         const float* x1 = view_row(p, slice, node, i, k + 1, k);
         const float* x0 = node == 0 ? view_row(p, slice, node, i, k, k) : nullptr;
         float g = 0.f, c = 0.f, q = 0.f;
-        for (int j = threadIdx.x; j < N; j += kElemThreads) {
-            const float xv = x1 ? x1[j] : 0.f;
-            const float pr = u[j] - xv;
+        auto update = [&](float uv, float xv, float& lv, float xo) {
+            const float pr = uv - xv;
             g = fmaf(pr, pr, g);
-            l[j] = fmaf(p.rho, pr, l[j]);
+            lv = fmaf(p.rho, pr, lv);
             if (node == 0) {
-                const float xo = x0 ? x0[j] : 0.f;
                 c = fmaf(xv - xo, xv - xo, c);
                 q = fmaf(xo, xo, q);
+            }
+        };
+        if ((N & 3) == 0) {
+            // rows are 16-byte aligned: two float4 of u, x and lambda per thread are
+            // loaded before any store, so the loads of a row are in flight together
+            const int N4 = N >> 2;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = threadIdx.x; j < N4; j += 2 * kElemThreads) {
+                const int jb = j + kElemThreads;
+                const bool two = jb < N4;
+                const float4 ua = __ldg(reinterpret_cast<const float4*>(u) + j);
+                const float4 ub = two ? __ldg(reinterpret_cast<const float4*>(u) + jb) : z4;
+                const float4 xa = x1 ? __ldg(reinterpret_cast<const float4*>(x1) + j) : z4;
+                const float4 xb = (x1 && two) ? __ldg(reinterpret_cast<const float4*>(x1) + jb) : z4;
+                float4 la = reinterpret_cast<const float4*>(l)[j];
+                float4 lb = two ? reinterpret_cast<const float4*>(l)[jb] : z4;
+                float4 oa = z4, ob = z4;
+                if (node == 0 && x0) {
+                    oa = __ldg(reinterpret_cast<const float4*>(x0) + j);
+                    if (two) ob = __ldg(reinterpret_cast<const float4*>(x0) + jb);
+                }
+                update(ua.x, xa.x, la.x, oa.x);
+                update(ua.y, xa.y, la.y, oa.y);
+                update(ua.z, xa.z, la.z, oa.z);
+                update(ua.w, xa.w, la.w, oa.w);
+                reinterpret_cast<float4*>(l)[j] = la;
+                if (two) {
+                    update(ub.x, xb.x, lb.x, ob.x);
+                    update(ub.y, xb.y, lb.y, ob.y);
+                    update(ub.z, xb.z, lb.z, ob.z);
+                    update(ub.w, xb.w, lb.w, ob.w);
+                    reinterpret_cast<float4*>(l)[jb] = lb;
+                }
+            }
+        } else {
+            for (int j = threadIdx.x; j < N; j += kElemThreads) {
+                float lv = l[j];
+                update(u[j], x1 ? x1[j] : 0.f, lv, x0 ? x0[j] : 0.f);
+                l[j] = lv;
             }
         }
         gap += g;
