@@ -1,5 +1,6 @@
 // Discrete parallel-beam x-ray transform on GB300 (sm_103a):
-//   - the per-angle trig table in constant memory,
+//   - host-built per-angle tables (int64 fixed-point positions, trapezoid
+//     constants) in device memory, copied into shared memory ahead of use,
 //   - the ray-driven projector (image chunks staged in shared memory),
 //   - the pixel-driven matched backprojector (sinogram windows staged in
 //     shared memory) with a plain epilogue and the fused Algorithm 2 u-step,
@@ -119,7 +120,7 @@ static BpConst make_bp_const(int N, int B, double c, double s) {
     r.C25 = (int)std::llrint(c * kFix25);
     r.S25 = (int)std::llrint(s * kFix25);
     r.CX16 = (int)std::llrint(16.0 * c * kFix25);
-    r.SY16 = (int)std::llrint(16.0 * s * kFix25);
+    r.SY8 = (int)std::llrint(8.0 * s * kFix25);
     const double gam = mn > 0.0 ? 1.0 / mn : (double)kGammaCap;
     r.gam = (float)gam;
     r.wf0 = (float)(0.5 + gam * (0.5 * mx + 1.0));
@@ -134,7 +135,7 @@ struct __align__(16) BpAngle {
     unsigned P0;    // bin coordinate of the tile's first pixel minus w0 (2^-25)
     int C25, S25;   // steps of one pixel in x and y (2^-25)
     float gam, wf0, wf1;
-    int CX16, SY16; // steps of 16 pixels, rounded once (not 16 rounded single steps)
+    int CX16, SY8;  // steps of 16 pixels in x and 8 in y, rounded once (not rounded single steps)
 };
 
 // what the copies of a chunk's windows need per angle
@@ -159,7 +160,7 @@ __device__ __forceinline__ void bp_tile_angle(BpAngle& r, BpWin& wv, const BpCon
     r.wf0 = k.wf0;
     r.wf1 = k.wf1;
     r.CX16 = k.CX16;
-    r.SY16 = k.SY16;
+    r.SY8 = k.SY8;
     wv.w0 = w0;
     wv.h = k.h;
 }
@@ -507,9 +508,12 @@ __device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, i
 // i + 2 and the descriptor of the item three items ahead are in flight, and
 // the queue has already been asked for the item after that. An item's
 // epilogue (Algorithm 2 step or store) overlaps the next chunk's copies.
-// 16 x 16 threads; thread (tx, ty) owns the 4 x 4 pixels (x0 + tx + 16 kx,
-// y0 + ty + 16 ky): a half-warp (16 consecutive tx) reads 16 window pairs
+// 16 x 8 threads; thread (tx, ty) owns the 4 x 8 pixels (x0 + tx + 16 kx,
+// y0 + ty + 8 ky): a half-warp (16 consecutive tx) reads 16 window pairs
 // within 16 consecutive entries, so its 64-bit shared loads never conflict.
+// A pixel's two candidate bins accumulate in the two lanes of one packed FP32
+// pair (one __ffma2_rn per pixel and angle), added together in the epilogue;
+// 32 pixels per thread spread the per-angle setup over more updates.
 template <int EPI>
 __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
     extern __shared__ __align__(16) unsigned char bp_dyn[];
@@ -584,11 +588,11 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         if (p.view.held) held = p.view.held + (size_t)(kiter - *p.view.k_first) * 2 * p.view.M * p.view.M;
     }
 
-    float acc[4][4];
+    float2 acc2[8][4];
 #pragma unroll
-    for (int ky = 0; ky < 4; ++ky)
+    for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
+        for (int kx = 0; kx < 4; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
 
     for (;;) {
         cp_async_wait<0>();
@@ -644,9 +648,9 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
             // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
             const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
-            const unsigned cx = (unsigned)A.CX16, sy = (unsigned)A.SY16;
+            const unsigned cx = (unsigned)A.CX16, sy = (unsigned)A.SY8;
 #pragma unroll
-            for (int ky = 0; ky < 4; ++ky) {
+            for (int ky = 0; ky < 8; ++ky) {
                 const unsigned prow = pb - (unsigned)ky * sy;
 #pragma unroll
                 for (int kx = 0; kx < 4; ++kx) {
@@ -655,19 +659,23 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
                     const float w0 = __saturatef(fmaf(-gam, F, wf0));
                     const float w1 = __saturatef(fmaf(gam, F, wf1));
-                    acc[ky][kx] = fmaf(w0, r.x, acc[ky][kx]);
-                    acc[ky][kx] = fmaf(w1, r.y, acc[ky][kx]);
+                    acc2[ky][kx] = __ffma2_rn(make_float2(w0, w1), r, acc2[ky][kx]);
                 }
             }
         }
 
         if (a0 + kBpChunk >= cur.na) {  // the item's last chunk: epilogue
             const int x0 = cur.tx * kBpTileX, y0 = cur.ty * kBpTileY;
+            float acc[8][4];
+#pragma unroll
+            for (int ky = 0; ky < 8; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = acc2[ky][kx].x + acc2[ky][kx].y;
             if (EPI == EPI_STORE) {
                 float* img = p.img + (size_t)cur.img * n;
 #pragma unroll
-                for (int ky = 0; ky < 4; ++ky) {
-                    const int row = y0 + ty + 16 * ky;
+                for (int ky = 0; ky < 8; ++ky) {
+                    const int row = y0 + ty + 8 * ky;
                     if (row >= N) continue;
 #pragma unroll
                     for (int kx = 0; kx < 4; ++kx) {
@@ -685,10 +693,10 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 const float eta = V.eta1[cur.node];
                 float* u = V.u + (size_t)cur.img * n;
                 const float* lam = V.lam + (size_t)cur.img * n;
-                const float* xrow[4];
+                const float* xrow[8];
 #pragma unroll
-                for (int ky = 0; ky < 4; ++ky) {
-                    const int row = min(y0 + ty + 16 * ky, N - 1);
+                for (int ky = 0; ky < 8; ++ky) {
+                    const int row = min(y0 + ty + 8 * ky, N - 1);
                     if (V.xnode) {  // consensus variant: the node's own x
                         xrow[ky] = V.xnode + (size_t)cur.img * n + (size_t)row * N;
                         continue;
@@ -702,8 +710,8 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 // per row: the 12 loads first, then the updates and stores (a store to u
                 // may alias a later load, so loads are not moved past stores by the compiler)
 #pragma unroll
-                for (int ky = 0; ky < 4; ++ky) {
-                    const int row = y0 + ty + 16 * ky;
+                for (int ky = 0; ky < 8; ++ky) {
+                    const int row = y0 + ty + 8 * ky;
                     if (row >= N) continue;
                     float* ur = u + (size_t)row * N;
                     const float* lr = lam + (size_t)row * N;
@@ -731,9 +739,9 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
                     __syncthreads();
 #pragma unroll
-                    for (int ky = 0; ky < 4; ++ky)
+                    for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-                        for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 16 * ky] = acc[ky][kx];
+                        for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 8 * ky] = acc[ky][kx];
                     __syncthreads();
                     float* ut = V.uT + (size_t)cur.img * n;
 #pragma unroll
@@ -745,9 +753,9 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 }
             }
 #pragma unroll
-            for (int ky = 0; ky < 4; ++ky)
+            for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = 0.f;
+                for (int kx = 0; kx < 4; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
         }
         if (!v1) break;
         j = j1;

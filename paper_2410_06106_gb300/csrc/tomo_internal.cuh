@@ -104,7 +104,7 @@ constexpr int kProjWMax = 252;   // max staged minor extent; + 3 for the 16-byte
 constexpr int kProjMaxNa = 4;
 constexpr int kProjStageFloats = kProjRows * kProjPitch;  // one 32 KB stage; two stages in flight
 
-constexpr int kBpThreads = 256;
+constexpr int kBpThreads = 128;
 constexpr int kBpTileX = 64, kBpTileY = 64;
 constexpr int kBpChunk = 32;  // angles staged per pass
 constexpr int kBpWin = 96;    // window pairs per angle: 63 (|c| + |s|) + 6 < 96
@@ -142,7 +142,7 @@ struct __align__(16) BpConst {
     float wf0, wf1;
     float h;         // 1 / max(|c|, |s|)
     int row;         // sinogram line of this entry (relative to the item's line base)
-    int CX16, SY16;  // steps of 16 pixels in x and y, rounded once (2^-25)
+    int CX16, SY8;   // steps of 16 pixels in x and 8 in y, rounded once (2^-25)
     int pad;
 };
 static_assert(sizeof(BpConst) == 64, "BpConst is copied in 16-byte pieces");
