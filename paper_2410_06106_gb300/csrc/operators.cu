@@ -293,25 +293,26 @@ __device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjA
     return acc.x + acc.y;
 }
 
-// staged minor range of chunk m0 of the item: extremes over its corner rays
-// (warp 0; lane 0 returns q0, the first staged column, 16-byte aligned)
-__device__ __forceinline__ int proj_chunk_q0(const ProjAngle* sa, int na, int b0, int blast, int m0, int lane,
-                                             int* w_out) {
+// staged minor ranges of chunks c0 .. c0 + 31 of the item (warp 0, lane L:
+// chunk c0 + L), written to the ring q0r[chunk & 63]: the first staged column
+// (16-byte aligned) from the lowest corner position over the item's angles;
+// an extent beyond the stage sets *bad (unreachable: the host bounds it)
+__device__ __forceinline__ void proj_q0_batch(const ProjAngle* sa, int na, int b0, int blast, int m_lo, int c0,
+                                              int nch, int lane, int* q0r, int* bad) {
+    const int c = c0 + lane;
+    if (c >= nch) return;
+    const long long m0 = m_lo + c * kProjRows, m1 = m0 + kProjRows - 1;
     long long lo = LLONG_MAX, hi = LLONG_MIN;
-    if (lane < 4 * na) {
-        const ProjAngle& C = sa[lane >> 2];
-        const int bb = (lane & 1) ? blast : b0;
-        const int mm = (lane & 2) ? m0 + kProjRows - 1 : m0;
-        lo = hi = (long long)bb * C.Db + (long long)mm * C.Dm + C.K0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    for (int a = 0; a < na; ++a) {
+        const ProjAngle& C = sa[a];
+        const long long pb0 = (long long)b0 * C.Db, pb1 = (long long)blast * C.Db;
+        const long long pm0 = m0 * C.Dm, pm1 = m1 * C.Dm;
+        lo = min(lo, min(pb0, pb1) + min(pm0, pm1) + C.K0);  // the corners are separable in b and m
+        hi = max(hi, max(pb0, pb1) + max(pm0, pm1) + C.K0);
     }
     const int q0 = ((int)(lo >> 40) - 2) & ~3;
-    *w_out = (int)(hi >> 40) + 3 - q0;
-    return q0;
+    q0r[c & 63] = q0;
+    if ((int)(hi >> 40) + 3 - q0 > kProjWMax + 3) atomicOr(bad, 1);
 }
 
 __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_constant__ ProjParams p) {
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
     float* stage = reinterpret_cast<float*>(proj_dyn);  // [2][kProjRows][kProjPitch]
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ ProjAngle sa[kProjMaxNa];
-    __shared__ int s_item, s_q0[2], s_bad;
+    __shared__ int s_item, s_q0[64], s_bad;  // s_q0: staged range per chunk, a ring of 64
     __shared__ float s_part[kProjThreads / 2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, B = p.B;
@@ -365,38 +366,32 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
         const int nch = item.nchunks;
         float total = 0.f;
 
-        if (warp == 0 && nch > 0) {  // chunk 0: range, and its load when TMA is available
-            int w;
-            const int q0 = proj_chunk_q0(sa, na, item.b0, blast, item.m_lo, lane, &w);
-            if (lane == 0) {
-                s_q0[0] = q0;
-                if (w > kProjWMax + 3) atomicOr(&s_bad, 1);  // unreachable: the host bounds the extent
-                if (tma) {
-                    fence_proxy_async();
-                    tma_load_box(stage, map, q0, item.m_lo, item.img, &bars[0], 4 * kProjStageFloats);
-                }
+        if (warp == 0 && nch > 0) {  // ranges of chunks 0..31; chunk 0's load when TMA is available
+            proj_q0_batch(sa, na, item.b0, blast, item.m_lo, 0, nch, lane, s_q0, &s_bad);
+            __syncwarp();
+            if (lane == 0 && tma) {
+                fence_proxy_async();
+                tma_load_box(stage, map, s_q0[0], item.m_lo, item.img, &bars[0], 4 * kProjStageFloats);
             }
         }
         for (int ch = 0; ch < nch; ++ch, pos += dpos) {
             const int sb = ch & 1;
             float* tile = stage + sb * kProjStageFloats;
             const int m0 = item.m_lo + ch * kProjRows;
-            __syncthreads();  // chunk ch-1 consumed by every thread; s_q0[sb] visible
+            __syncthreads();  // chunk ch-1 consumed by every thread; s_q0[ch & 63] visible
             if (s_bad) break;
-            if (warp == 0 && ch + 1 < nch) {  // next chunk: range and (TMA) load into the other stage
-                int w;
-                const int q1 = proj_chunk_q0(sa, na, item.b0, blast, m0 + kProjRows, lane, &w);
-                if (lane == 0) {
-                    s_q0[sb ^ 1] = q1;
-                    if (w > kProjWMax + 3) atomicOr(&s_bad, 1);
-                    if (tma) {
-                        fence_proxy_async();
-                        tma_load_box(stage + (sb ^ 1) * kProjStageFloats, map, q1, m0 + kProjRows, item.img,
-                                     &bars[sb ^ 1], 4 * kProjStageFloats);
-                    }
+            if (warp == 0 && ch + 1 < nch) {  // next chunk: (TMA) load into the other stage
+                if (((ch + 1) & 31) == 0) {  // ranges of the next 32 chunks (entries 32 back are done)
+                    proj_q0_batch(sa, na, item.b0, blast, item.m_lo, ch + 1, nch, lane, s_q0, &s_bad);
+                    __syncwarp();
+                }
+                if (lane == 0 && tma) {
+                    fence_proxy_async();
+                    tma_load_box(stage + (sb ^ 1) * kProjStageFloats, map, s_q0[(ch + 1) & 63], m0 + kProjRows,
+                                 item.img, &bars[sb ^ 1], 4 * kProjStageFloats);
                 }
             }
-            const int q0 = s_q0[sb];
+            const int q0 = s_q0[ch & 63];
             if (tma) {
                 const unsigned ph = sb ? (uses1++ & 1u) : (uses0++ & 1u);
                 if (!mbar_wait(&bars[sb], ph)) {  // a load that never lands: give up on the launch
@@ -514,6 +509,22 @@ __device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, i
 // A pixel's two candidate bins accumulate in the two lanes of one packed FP32
 // pair (one __ffma2_rn per pixel and angle), added together in the epilogue;
 // 32 pixels per thread spread the per-angle setup over more updates.
+// row `row` of the view of x that Algorithm 2 reads for the item's node: the
+// node's own x (consensus variant), else the message-ring plane of the version
+// the node holds of the row's segment (null before any message arrived)
+__device__ __forceinline__ const float* bp_view_row(const BpView& V, const BpItem& it, int row, const int32_t* held,
+                                                    int kiter, size_t n, int N) {
+    if (V.xnode) return V.xnode + (size_t)it.img * n + (size_t)row * N;
+    const int mi = it.node * V.M + V.seg_of_row[row];
+    const int jj = held ? held[mi] : kiter - V.lag[mi];
+    return jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + it.slice) * n) + (size_t)row * N
+                   : nullptr;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ptr));
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
     extern __shared__ __align__(16) unsigned char bp_dyn[];
@@ -639,6 +650,21 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             issue_desc(slot, __shfl_sync(0xffffffffu, idx, 0));
         }
         cp_async_commit();
+        if (EPI == EPI_USTEP && a0 + kBpChunk >= cur.na) {
+            // the epilogue follows this chunk: bring its rows of u, lambda and the view
+            // of x into L2 now (two 128-byte lines per 64-pixel row; a hint, no data moves
+            // to registers), so that its loads do not wait on DRAM
+            static_assert(kBpThreads == 2 * kBpTileY && kBpTileX == 64, "two threads per tile row");
+            const int row = cur.ty * kBpTileY + (tid >> 1);
+            const int col = cur.tx * kBpTileX + 32 * (tid & 1);
+            if (row < N && col < N) {
+                const size_t o = (size_t)cur.img * n + (size_t)row * N + col;
+                prefetch_l2(p.view.u + o);
+                prefetch_l2(p.view.lam + o);
+                const float* xr = bp_view_row(p.view, cur, row, held, kiter, n, N);
+                if (xr) prefetch_l2(xr + col);
+            }
+        }
 
         const float2* win = wins + buf * kBpStageFloat2;
         const BpAngle* sab = s_a[buf];
@@ -695,18 +721,8 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 const float* lam = V.lam + (size_t)cur.img * n;
                 const float* xrow[8];
 #pragma unroll
-                for (int ky = 0; ky < 8; ++ky) {
-                    const int row = min(y0 + ty + 8 * ky, N - 1);
-                    if (V.xnode) {  // consensus variant: the node's own x
-                        xrow[ky] = V.xnode + (size_t)cur.img * n + (size_t)row * N;
-                        continue;
-                    }
-                    const int mi = cur.node * V.M + V.seg_of_row[row];
-                    const int jj = held ? held[mi] : kiter - V.lag[mi];
-                    xrow[ky] = jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + cur.slice) * n) +
-                                             (size_t)row * N
-                                       : nullptr;
-                }
+                for (int ky = 0; ky < 8; ++ky)
+                    xrow[ky] = bp_view_row(V, cur, min(y0 + ty + 8 * ky, N - 1), held, kiter, n, N);
                 // per row: the 12 loads first, then the updates and stores (a store to u
                 // may alias a later load, so loads are not moved past stores by the compiler)
 #pragma unroll
