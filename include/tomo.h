@@ -88,6 +88,8 @@ TOMO_API tomo_status tomo_geometry_destroy(tomo_geometry_t g);
  *                             then n_sel must equal n_angles); read during
  *                             the call only
  * subtract [batch][n_sel][B]  device or NULL (the data term d of Alg. 2)
+ * Requires 1 <= n_sel <= 65536 and batch >= 1 (an empty request is an
+ * argument error, TOMO_ERR_INVALID_ARG, with nothing launched).
  * Ray-driven kernel, FP32 arithmetic, FP32 accumulation. */
 TOMO_API tomo_status tomo_project(tomo_geometry_t g, const float* img, float* sino,
                          const int32_t* angle_idx, int n_sel, int batch,
@@ -102,7 +104,8 @@ TOMO_API tomo_status tomo_project(tomo_geometry_t g, const float* img, float* si
  * device image instead of memory the library allocates, so the call performs
  * no cudaMalloc/cudaFree and no allocating library routine.
  * Limits: n_sel <= 8192 angles and at most 16384 work items (about
- * batch * ceil(n_sel / 4) * ceil(B / 64)); larger requests return
+ * batch * ceil(n_sel / 4) * ceil(B / 128); up to batch * n_sel * ceil(B / 128)
+ * when consecutive angles cannot share an item); larger requests return
  * TOMO_ERR_WORKSPACE with a message and launch nothing. The array (576 KiB)
  * is held on every GPU that loads the library until the process exits.
  * The first call on each device looks up the array's device address; make

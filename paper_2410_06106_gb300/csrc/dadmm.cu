@@ -34,6 +34,7 @@ namespace tomo {
 void prepare_codecs(int km_k);
 
 constexpr int kStatsCap = 1024;   // statistics ring (iterations)
+constexpr int kGraphCache = 4;    // captured iterations kept per handle
 constexpr int kDualPerNode = 8;   // dual-kernel blocks per (slice, node)
 constexpr int kResPerSlice = 64;  // residual-norm blocks per slice
 constexpr int kElemThreads = 256;
@@ -98,8 +99,18 @@ struct Dadmm {
     // stream / graph
     cudaStream_t own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<const void*> gkey;
+    // captured iterations, one per set of state, workspace and input pointers, least
+    // recently used first (a caller that alternates a few input buffers does not
+    // re-capture)
+    struct Captured {
+        std::vector<const void*> key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Captured> graphs;
+    void drop_graphs() {
+        for (Captured& c : graphs) cudaGraphExecDestroy(c.exec);
+        graphs.clear();
+    }
     // phase timing
     bool profiling = false;
     std::vector<cudaEvent_t> pev;  // num_phases + 1 boundaries
@@ -618,7 +629,7 @@ static void relay_tables(int M, const std::vector<int32_t>& adj, std::vector<int
 
 static void free_dadmm(Dadmm* h) {
     if (!h) return;
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->drop_graphs();
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->own) cudaStreamDestroy(h->own);
@@ -1383,10 +1394,7 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
         // u-step epilogue
         const bool maps = make_image_map(&h.map_u, st->u, h.N, h.S * h.M) &&
                           make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
-        if (maps != (h.has_maps != 0) && h.gexec) {
-            TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
-            h.gexec = nullptr;
-        }
+        if (maps != (h.has_maps != 0)) h.drop_graphs();
         h.has_maps = maps ? 1 : 0;
         if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
             launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
@@ -1397,10 +1405,14 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
                                                   w.resid, (const void*)(uintptr_t)(h.lossy ? 1 : 0)};
-            if (!h.gexec || key != h.gkey) {
-                if (h.gexec) {
-                    TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
-                    h.gexec = nullptr;
+            size_t gi = 0;
+            while (gi < h.graphs.size() && h.graphs[gi].key != key) ++gi;
+            if (gi < h.graphs.size()) {  // most recently used last
+                std::rotate(h.graphs.begin() + gi, h.graphs.begin() + gi + 1, h.graphs.end());
+            } else {
+                if (h.graphs.size() >= kGraphCache) {
+                    TOMO_CUDA(cudaGraphExecDestroy(h.graphs.front().exec));
+                    h.graphs.erase(h.graphs.begin());
                 }
                 cudaGraph_t graph = nullptr;
                 TOMO_CUDA(cudaStreamBeginCapture(h.own, cudaStreamCaptureModeThreadLocal));
@@ -1412,14 +1424,16 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
                     throw;
                 }
                 TOMO_CUDA(cudaStreamEndCapture(h.own, &graph));
-                cudaError_t e = cudaGraphInstantiate(&h.gexec, graph, 0);
+                cudaGraphExec_t exec = nullptr;
+                cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
                 cudaGraphDestroy(graph);
                 TOMO_CUDA(e);
-                h.gkey = key;
+                h.graphs.push_back({key, exec});
             }
+            cudaGraphExec_t gexec = h.graphs.back().exec;
             TOMO_CUDA(cudaEventRecord(h.ev_in, user));
             TOMO_CUDA(cudaStreamWaitEvent(h.own, h.ev_in, 0));
-            for (int it = 0; it < n_iters; ++it) TOMO_CUDA(cudaGraphLaunch(h.gexec, h.own));
+            for (int it = 0; it < n_iters; ++it) TOMO_CUDA(cudaGraphLaunch(gexec, h.own));
             TOMO_CUDA(cudaEventRecord(h.ev_out, h.own));
             TOMO_CUDA(cudaStreamWaitEvent(user, h.ev_out, 0));
         } else {
@@ -1497,10 +1511,7 @@ tomo_status dadmm_set_profiling(dadmm_t hh, int enable) {
             for (auto& e : h.pev) TOMO_CUDA(cudaEventCreate(&e));
         }
         h.profiling = enable != 0;
-        if (h.gexec) {  // the next step re-captures with or without the event nodes
-            TOMO_CUDA(cudaGraphExecDestroy(h.gexec));
-            h.gexec = nullptr;
-        }
+        h.drop_graphs();  // the next step re-captures with or without the event nodes
     });
 }
 

@@ -251,9 +251,9 @@ __global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
 // ------------------------------------------------------------------
 
 // thread -> (angle slot, bin offset, row group) of an item:
-// na = 4: 4 angles x 64 bins, warp w takes bins 16 (w & 3) .. + 16 of angles
+// na = 4: 4 angles x 128 bins, warp w takes bins 16 (w & 3) .. + 16 of angles
 //         2 (w >> 2) and + 1 (half-warps of adjacent angles read nearly the
-//         same shared words);
+//         same shared words), and the same bins + 64: two rays per thread;
 // na = 2: 2 angles x 128 bins, warp w takes bins 16 w .. + 16 of both;
 // na = 1: 128 bins x 2 row groups (threads 128..255 take rows 16..31 of
 //         every chunk; the two partial sums are added at the end).
@@ -273,7 +273,7 @@ __device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& b
     }
 }
 
-__device__ __forceinline__ int proj_bins(int na) { return na == 1 ? 128 : kProjThreads / na; }
+constexpr int kProjItemBins = 128;  // bins of an item: every item holds 128 bins of each of its angles
 
 // NR consecutive rows of one ray inside a staged chunk: the two candidate
 // pixels of each row, weighted by the trapezoid (see the file header); the
@@ -291,6 +291,25 @@ __device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjA
         acc = __ffma2_rn(make_float2(w0, w1), make_float2(t[0], t[1]), acc);
     }
     return acc.x + acc.y;
+}
+
+// two rays of one angle over the same NR rows, interleaved row by row
+template <int NR>
+__device__ __forceinline__ float2 ray_rows2(const float* base0, int f0, const float* base1, int f1,
+                                            const ProjAngle& A) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int p0 = f0 + r * A.dm25, p1 = f1 + r * A.dm25;
+        const float F0 = one_plus_frac25(p0), F1 = one_plus_frac25(p1);
+        const float* t0 = base0 + r * kProjPitch + (p0 >> kFracBits);
+        const float* t1 = base1 + r * kProjPitch + (p1 >> kFracBits);
+        acc0 = __ffma2_rn(make_float2(__saturatef(fmaf(-A.kappa, F0, A.wf0)), __saturatef(fmaf(A.kappa, F0, A.wf1))),
+                          make_float2(t0[0], t0[1]), acc0);
+        acc1 = __ffma2_rn(make_float2(__saturatef(fmaf(-A.kappa, F1, A.wf0)), __saturatef(fmaf(A.kappa, F1, A.wf1))),
+                          make_float2(t1[0], t1[1]), acc1);
+    }
+    return make_float2(acc0.x + acc0.y, acc1.x + acc1.y);
 }
 
 // staged minor ranges of chunks c0 .. c0 + 31 of the item (warp 0, lane L:
@@ -315,7 +334,7 @@ __device__ __forceinline__ void proj_q0_batch(const ProjAngle* sa, int na, int b
     if ((int)(hi >> 40) + 3 - q0 > kProjWMax + 3) atomicOr(bad, 1);
 }
 
-__global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_constant__ ProjParams p) {
+__global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_constant__ ProjParams p) {
     extern __shared__ __align__(1024) unsigned char proj_dyn[];
     float* stage = reinterpret_cast<float*>(proj_dyn);  // [2][kProjRows][kProjPitch]
     __shared__ __align__(8) uint64_t bars[2];
@@ -352,8 +371,10 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
         int slot, boff, rgrp;
         proj_lane_map(na, tid, slot, boff, rgrp);
         const int b = item.b0 + boff;
-        const int blast = min(item.b0 + proj_bins(na) - 1, B - 1);
+        const int blast = min(item.b0 + kProjItemBins - 1, B - 1);
         const int bc = min(b, blast);  // rays past the last bin shadow it (their output is dropped)
+        const bool two = na == 4;      // a second ray, 64 bins further
+        const int b2 = b + 64, bc2 = min(b2, blast);
         const ProjAngle A = sa[slot];
         const int colmaj = sa[0].colmaj;
         const bool tma = colmaj ? p.has_mapT : p.has_map;
@@ -362,9 +383,10 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
         // this ray's position at the first row of its row group in chunk 0
         const int r0 = rgrp * (kProjRows / 2);
         long long pos = (long long)bc * A.Db + (long long)(item.m_lo + r0) * A.Dm + A.K0;
+        long long pos2 = (long long)bc2 * A.Db + (long long)(item.m_lo + r0) * A.Dm + A.K0;
         const long long dpos = (long long)kProjRows * A.Dm;
         const int nch = item.nchunks;
-        float total = 0.f;
+        float total = 0.f, total2 = 0.f;
 
         if (warp == 0 && nch > 0) {  // ranges of chunks 0..31; chunk 0's load when TMA is available
             proj_q0_batch(sa, na, item.b0, blast, item.m_lo, 0, nch, lane, s_q0, &s_bad);
@@ -374,7 +396,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
                 tma_load_box(stage, map, s_q0[0], item.m_lo, item.img, &bars[0], 4 * kProjStageFloats);
             }
         }
-        for (int ch = 0; ch < nch; ++ch, pos += dpos) {
+        for (int ch = 0; ch < nch; ++ch, pos += dpos, pos2 += dpos) {
             const int sb = ch & 1;
             float* tile = stage + sb * kProjStageFloats;
             const int m0 = item.m_lo + ch * kProjRows;
@@ -438,7 +460,15 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
             const int J = (int)(pos >> 40);
             const int f0 = (int)((pos >> (40 - kFracBits)) & ((1 << kFracBits) - 1));
             const float* base = tile + r0 * kProjPitch + (J - q0);
-            total += (na == 1) ? ray_rows<kProjRows / 2>(base, f0, A) : ray_rows<kProjRows>(base, f0, A);
+            if (two) {
+                const int J2 = (int)(pos2 >> 40);
+                const int f2 = (int)((pos2 >> (40 - kFracBits)) & ((1 << kFracBits) - 1));
+                const float2 t = ray_rows2<kProjRows>(base, f0, tile + (J2 - q0), f2, A);
+                total += t.x;
+                total2 += t.y;
+            } else {
+                total += (na == 1) ? ray_rows<kProjRows / 2>(base, f0, A) : ray_rows<kProjRows>(base, f0, A);
+            }
         }
         if (s_bad) {  // wait (bounded) for a load still in flight before leaving
             if (tid == 0 && tma) {
@@ -460,6 +490,12 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(const __grid_cons
             if (p.sub) v -= __ldg(p.sub + o);
             if (p.prescale) v *= A.h;
             p.out[o] = v;
+            if (two && b2 < B) {
+                float v2 = A.h * total2;
+                if (p.sub) v2 -= __ldg(p.sub + o + 64);
+                if (p.prescale) v2 *= A.h;
+                p.out[o + 64] = v2;
+            }
         }
         __syncthreads();  // sa / s_item / s_q0 reused by the next item
     }
@@ -998,7 +1034,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
             // extent check over every bin run and chunk
             std::vector<HostProj> As;
             for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-            const int wb = na == 1 ? 128 : kProjThreads / na;
+            const int wb = kProjItemBins;
             bool ok = true;
             for (int b0 = 0; b0 < g.B && ok; b0 += wb) {
                 const int b1 = std::min(b0 + wb - 1, g.B - 1);
@@ -1021,7 +1057,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
                                            std::to_string(angs[i].angle) + ")");
         std::vector<HostProj> As;
         for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-        const int wb = na == 1 ? 128 : kProjThreads / na;
+        const int wb = kProjItemBins;
         for (int b0 = 0; b0 < g.B; b0 += wb) {
             const int b1 = std::min(b0 + wb - 1, g.B - 1);
             int lo = g.N, hi = -1;

@@ -73,8 +73,8 @@ struct AngRow {
 };
 
 // projector work item: na consecutive entries of an AngRow list that share
-// the major axis, a run of 256/na bins, the major-index range covering every
-// ray of the item, processed in chunks of kProjRows rows/columns
+// the major axis, a run of 128 bins of each, the major-index range covering
+// every ray of the item, processed in chunks of kProjRows rows/columns
 struct ProjItem {
     int img;      // image index (units of N*N floats)
     int outb;     // output row base (added to AngRow::row)
