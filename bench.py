@@ -278,6 +278,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(args.warmup):
             s.step(sino, 1, stats=False)
         torch.cuda.synchronize()
+        shape = s.launch_shape()  # chosen by the first step (autotuned launch shapes)
         names = s.phase_names()
         clocks = ClockSampler(local)
         clocks.start()
@@ -398,7 +399,8 @@ def run_ours(args, ws, rank, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded random-ellipse phantoms, analytic sinograms, 1% noise)",
                 "config": dict(workload_config(args.workload, args.slices), parallelism="replicas" if ws > 1 else "single",
-                               mode="batched persistent, graph-captured"),
+                               mode="batched persistent, graph-captured",
+                               launch_shape={"bp_tile_x": shape[0], "proj_item_bins": shape[1], "tune": "auto"}),
                 "plain": plain, "e2e": e2e,
                 "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_tflops,
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,

@@ -39,6 +39,7 @@ class DadmmConfig(C.Structure):
         ("eta2", C.c_double), ("rho", C.c_double), ("E1", C.c_int), ("E2", C.c_int),
         ("km_k", C.c_int), ("km_iters", C.c_int), ("jpeg_quality", C.c_int),
         ("seed", C.c_uint64), ("mode", C.c_int), ("max_stale", C.c_int), ("variant", C.c_int),
+        ("tune", C.c_int),
     ]
 
 
@@ -73,6 +74,7 @@ SIGNATURES = {
     "dadmm_create": (C.c_int, [C.c_void_p, C.POINTER(DadmmConfig), C.c_void_p]),
     "dadmm_destroy": (C.c_int, [C.c_void_p]),
     "dadmm_ring_depth": (C.c_int, [C.c_void_p]),
+    "dadmm_launch_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dadmm_state_size": (C.c_size_t, [C.c_void_p]),
     "dadmm_state_init": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p]),
     "dadmm_workspace_size": (C.c_size_t, [C.c_void_p]),
@@ -305,7 +307,9 @@ class DADMM:
     xseg, hist, iter) and the workspace are torch tensors owned by this object.
     """
 
-    def __init__(self, prob, eta1, mode="batched", geometry=None):
+    def __init__(self, prob, eta1, mode="batched", geometry=None, tune="auto"):
+        """tune: launch shapes, "auto" (timed at the first step, cached per
+        problem shape in the process), "wide" or "narrow" (see dadmm_config)"""
         g = prob["geometry"]
         self.N, self.B, self.A = g["N"], g["B"], g["A"]
         self.S, self.M = int(prob["S"]), int(prob["M"])
@@ -337,6 +341,10 @@ class DADMM:
         if self.variant not in ("segments", "consensus"):
             raise TomoError(-1, "variant must be 'segments' or 'consensus'")
         cfg.variant = 1 if self.variant == "consensus" else 0
+        tunes = {"wide": 0, "auto": 1, "narrow": 2}
+        if tune not in tunes:
+            raise TomoError(-1, "tune must be 'auto', 'wide' or 'narrow'")
+        cfg.tune = tunes[tune]
         self.mode = mode
         self.cfg = cfg
         h = C.c_void_p()
@@ -423,6 +431,12 @@ class DADMM:
         out = out if out is not None else torch.empty(self.S, self.N, self.N, device="cuda")
         _check(lib().dadmm_home_view(self.handle, C.byref(self._state), _ptr(out), _stream()))
         return out
+
+    def launch_shape(self):
+        """(backprojector tile width, bins of 4-angle projector items) in use"""
+        tx, nb = C.c_int(), C.c_int()
+        _check(lib().dadmm_launch_shape(self.handle, C.byref(tx), C.byref(nb)))
+        return tx.value, nb.value
 
     @property
     def k(self):

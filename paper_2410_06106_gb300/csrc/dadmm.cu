@@ -23,6 +23,9 @@
 // with (k - lag) mod D; the iteration counter lives on the device so one
 // captured CUDA graph serves every iteration.
 #include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <numeric>
 #include <queue>
@@ -72,6 +75,13 @@ struct Dadmm {
     std::vector<int> km_slice_begin, jp_slice_begin;  // tasks are slice-major: per-(slice, owner) index
     std::vector<int> km_index, jp_index;              // [(slice*M + owner)] -> task index or -1
     int grid_proj = 0, grid_bp = 0;
+    // launch shapes (K9): backprojector tile width, bins of 4-angle projector items;
+    // tune: 0 wide shapes, 1 timed at the first step and cached per problem shape,
+    // 2 narrow shapes
+    int tune = 0, bp_tile_x = kBpTileXWide, proj_bins4 = kProjItemBins;
+    bool tuned = false;
+    std::vector<AngRow> angs;           // node-major angle list
+    std::vector<int32_t> node_ang_ptr;  // [M + 1]
     // workspace layout (byte offsets from the aligned base)
     size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_coefs = 0, off_bits = 0, off_dual = 0,
            off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
@@ -642,6 +652,51 @@ static void free_dadmm(Dadmm* h) {
     delete h;
 }
 
+// the projector and backprojector work lists of the handle's launch shapes, in
+// the plain (per slice and node) and batched forms; replaces earlier lists
+static void build_lists(Dadmm& h) {
+    const int M = h.M, S = h.S, A = h.A;
+    std::vector<ProjItem> pplain;
+    std::vector<BpItem> bplain;
+    h.p_range.assign((size_t)2 * S * M, 0);
+    h.b_range.assign((size_t)2 * S * M, 0);
+    for (int sl = 0; sl < S; ++sl)
+        for (int m = 0; m < M; ++m) {
+            const int a0 = h.node_ang_ptr[m], na = h.node_ang_ptr[m + 1] - a0;
+            const int sn = sl * M + m;
+            h.p_range[2 * sn] = (int)pplain.size();
+            if (na > 0) build_proj_items(*h.g, h.angs, a0, na, sn, sl * A, pplain, h.proj_bins4);
+            h.p_range[2 * sn + 1] = (int)pplain.size();
+            h.b_range[2 * sn] = (int)bplain.size();
+            if (na > 0) build_bp_items(*h.g, a0, na, sn, sl * A, m, sl, bplain, h.bp_tile_x);
+            h.b_range[2 * sn + 1] = (int)bplain.size();
+        }
+    // nodes without angles still need the u-step (pure proximal term)
+    for (int sl = 0; sl < S; ++sl)
+        for (int m = 0; m < M; ++m) {
+            const int sn = sl * M + m;
+            if (h.b_range[2 * sn] == h.b_range[2 * sn + 1]) {
+                build_bp_items(*h.g, h.node_ang_ptr[m], 0, sn, sl * A, m, sl, bplain, h.bp_tile_x);
+                h.b_range[2 * sn + 1] = (int)bplain.size();
+            }
+        }
+    // batched order: node-major, as the plain lists, so that the blocks in flight
+    // work on few nodes at a time and each node's image stays in L2
+    for (void* q : {(void*)h.d_pitems, (void*)h.d_bitems, (void*)h.d_pplain, (void*)h.d_bplain})
+        if (q) cudaFree(q);
+    h.d_pitems = h.d_pplain = nullptr;
+    h.d_bitems = h.d_bplain = nullptr;
+    h.d_pitems = device_upload(pplain);
+    h.d_bitems = device_upload(bplain);
+    h.d_pplain = device_upload(pplain);
+    h.d_bplain = device_upload(bplain);
+    h.n_pitems = (int)pplain.size();
+    h.n_bitems = (int)bplain.size();
+    h.grid_proj = persistent_grid_project();
+    h.grid_bp = persistent_grid_backproject(true, h.bp_tile_x);
+    h.drop_graphs();
+}
+
 struct WsPtrs {
     float* uT;
     float* resid;
@@ -704,26 +759,9 @@ static ElemParams elem_params(const Dadmm& h, const dadmm_state& st, const WsPtr
     return p;
 }
 
-// enqueue one full iteration on stream st
-static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w,
-                              cudaStream_t s) {
-    const bool batched = h.mode == DADMM_MODE_BATCHED;
-    int phase = 0;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    TOMO_CUDA(cudaStreamIsCapturing(s, &cap));
-    auto mark = [&]() {  // boundary before phase `phase`; a graph node when capturing
-        if (h.profiling)
-            TOMO_CUDA(cudaEventRecordWithFlags(h.pev[phase], s,
-                                               cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0));
-        ++phase;
-    };
-    const size_t SM = (size_t)h.S * h.M;
-    // per-iteration resets: work queues, segment min/max keys, JPEG counters
-    TOMO_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * (2 * h.E1 + 2), s));
-    TOMO_CUDA(cudaMemsetAsync(w.lo, 0xFF, sizeof(unsigned) * SM, s));
-    TOMO_CUDA(cudaMemsetAsync(w.hi, 0x00, sizeof(unsigned) * SM, s));
-    TOMO_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(long long) * SM, s));
-
+// projector launch parameters of the iteration: u -> h_a (h_a P u - d) in the
+// residual buffer (work list, queue counter and item count set by the caller)
+static ProjParams proj_params(const Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w) {
     ProjParams pp{};
     if (h.has_maps) {
         pp.map = h.map_u;
@@ -739,6 +777,11 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     pp.B = h.B;
     pp.ptab = h.g->d_ptab;
     pp.prescale = 1;  // the residual is stored as h_a r_a, the form the backprojector stages
+    return pp;
+}
+
+// backprojector (u-step) launch parameters of the iteration
+static BpParams bp_params(const Dadmm& h, const dadmm_state& st, const WsPtrs& w) {
     BpParams bp{};
     bp.sino = w.resid;
     bp.bk = h.d_bk;
@@ -762,6 +805,31 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
     bp.view.D = h.D;
     bp.view.S = h.S;
     bp.view.M = h.M;
+    return bp;
+}
+
+// enqueue one full iteration on stream st
+static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w,
+                              cudaStream_t s) {
+    const bool batched = h.mode == DADMM_MODE_BATCHED;
+    int phase = 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TOMO_CUDA(cudaStreamIsCapturing(s, &cap));
+    auto mark = [&]() {  // boundary before phase `phase`; a graph node when capturing
+        if (h.profiling)
+            TOMO_CUDA(cudaEventRecordWithFlags(h.pev[phase], s,
+                                               cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0));
+        ++phase;
+    };
+    const size_t SM = (size_t)h.S * h.M;
+    // per-iteration resets: work queues, segment min/max keys, JPEG counters
+    TOMO_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * (2 * h.E1 + 2), s));
+    TOMO_CUDA(cudaMemsetAsync(w.lo, 0xFF, sizeof(unsigned) * SM, s));
+    TOMO_CUDA(cudaMemsetAsync(w.hi, 0x00, sizeof(unsigned) * SM, s));
+    TOMO_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(long long) * SM, s));
+
+    ProjParams pp = proj_params(h, st, sino, w);
+    BpParams bp = bp_params(h, st, w);
 
     for (int e = 0; e < h.E1; ++e) {
         if (batched) {
@@ -774,7 +842,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
             bp.items = h.d_bitems;
             bp.n_items = h.n_bitems;
             bp.counter = w.counters + 2 * e + 1;
-            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s);
+            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x);
         } else {
             mark();
             for (int sn = 0; sn < h.S * h.M; ++sn) {
@@ -788,7 +856,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
                 bp.items = h.d_bplain + h.b_range[2 * sn];
                 bp.n_items = h.b_range[2 * sn + 1] - h.b_range[2 * sn];
                 bp.counter = nullptr;
-                launch_backproject_ustep(bp, bp.n_items, s);
+                launch_backproject_ustep(bp, bp.n_items, s, h.bp_tile_x);
             }
         }
     }
@@ -1119,43 +1187,18 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             // angle list (node-major), rows = natural angle index
             std::vector<AngRow> angs(A);
             for (int q = 0; q < A; ++q) angs[q] = AngRow{c.node_ang[q], c.node_ang[q]};
-            // work lists
-            std::vector<ProjItem> pplain;
-            std::vector<BpItem> bplain;
-            h->p_range.resize((size_t)2 * c.S * M);
-            h->b_range.resize((size_t)2 * c.S * M);
-            for (int sl = 0; sl < c.S; ++sl)
-                for (int m = 0; m < M; ++m) {
-                    const int a0 = c.node_ang_ptr[m], na = c.node_ang_ptr[m + 1] - a0;
-                    const int sn = sl * M + m;
-                    h->p_range[2 * sn] = (int)pplain.size();
-                    if (na > 0) build_proj_items(*g, angs, a0, na, sn, sl * A, pplain);
-                    h->p_range[2 * sn + 1] = (int)pplain.size();
-                    h->b_range[2 * sn] = (int)bplain.size();
-                    if (na > 0) build_bp_items(*g, a0, na, sn, sl * A, m, sl, bplain);
-                    h->b_range[2 * sn + 1] = (int)bplain.size();
-                }
-            // nodes without angles still need the u-step (pure proximal term)
-            for (int sl = 0; sl < c.S; ++sl)
-                for (int m = 0; m < M; ++m) {
-                    const int sn = sl * M + m;
-                    if (h->b_range[2 * sn] == h->b_range[2 * sn + 1]) {
-                        build_bp_items(*g, c.node_ang_ptr[m], 0, sn, sl * A, m, sl, bplain);
-                        h->b_range[2 * sn + 1] = (int)bplain.size();
-                    }
-                }
-            // batched order: node-major, as the plain lists, so that the blocks in flight
-            // work on few nodes at a time and each node's image stays in L2
-            std::vector<ProjItem> pb = pplain;
-            std::vector<BpItem> bb = bplain;
+            h->angs = angs;
+            h->node_ang_ptr.assign(c.node_ang_ptr, c.node_ang_ptr + M + 1);
             h->d_angs = device_upload(angs);
             h->d_bk = device_upload(bp_list_consts(*g, angs));
-            h->d_pitems = device_upload(pb);
-            h->d_bitems = device_upload(bb);
-            h->d_pplain = device_upload(pplain);
-            h->d_bplain = device_upload(bplain);
-            h->n_pitems = (int)pb.size();
-            h->n_bitems = (int)bb.size();
+            TOMO_REQUIRE(c.tune == DADMM_TUNE_WIDE || c.tune == DADMM_TUNE_AUTO || c.tune == DADMM_TUNE_NARROW,
+                         "unknown tune setting");
+            h->tune = c.tune;
+            if (c.tune == DADMM_TUNE_NARROW) {
+                h->bp_tile_x = kBpTileXNarrow;
+                h->proj_bins4 = kProjItemBinsNarrow;
+            }
+            build_lists(*h);
             // tables
             std::vector<int32_t> seg_of_row(N);
             for (int m = 0; m < M; ++m)
@@ -1206,9 +1249,6 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->d_jp = device_upload(jp);
             h->n_km = (int)km.size();
             h->n_jp = (int)jp.size();
-            // launch shapes
-            h->grid_proj = persistent_grid_project();
-            h->grid_bp = persistent_grid_backproject(true);
             prepare_codecs(c.km_k);
             // workspace layout
             size_t off = 0;
@@ -1251,6 +1291,15 @@ tomo_status dadmm_destroy(dadmm_t hh) {
 }
 
 int dadmm_ring_depth(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->D : 0; }
+
+tomo_status dadmm_launch_shape(dadmm_t hh, int* bp_tile_x, int* proj_item_bins) {
+    return guard([&] {
+        Dadmm& h = *as_dadmm(hh);
+        TOMO_REQUIRE(bp_tile_x && proj_item_bins, "output pointers must be non-NULL");
+        *bp_tile_x = h.bp_tile_x;
+        *proj_item_bins = h.proj_bins4;
+    });
+}
 
 size_t dadmm_state_size(dadmm_t hh) {
     if (!hh) return 0;
@@ -1319,6 +1368,117 @@ namespace tomo {
 
 // the held-version table of a lossy call: row i = (versions held at iteration k0+i, at k0+i+1);
 // refuses a mask under which a version read would have left the ring
+// process-wide choices of the launch shapes, keyed by the device and the
+// problem's shape (sizes, trig table, angle partition)
+static std::mutex g_shape_mu;
+static std::map<std::vector<long long>, std::pair<int, int>> g_shape_cache;
+
+static std::vector<long long> shape_key(const Dadmm& h) {
+    int dev = 0;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    std::vector<long long> k = {dev, h.N, h.B, h.A, h.S, h.M, h.has_maps};
+    uint64_t f = 1469598103934665603ULL;  // FNV-1a over the trig table, the angle list and the partition
+    auto mix = [&](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            f ^= (v >> (8 * b)) & 0xFF;
+            f *= 1099511628211ULL;
+        }
+    };
+    for (int a = 0; a < h.g->A; ++a) {
+        uint64_t u;
+        std::memcpy(&u, &h.g->c[a], 8);
+        mix(u);
+        std::memcpy(&u, &h.g->s[a], 8);
+        mix(u);
+    }
+    for (const AngRow& r : h.angs) mix((uint64_t)r.angle);
+    for (int32_t v : h.node_ang_ptr) mix((uint64_t)v);
+    k.push_back((long long)f);
+    return k;
+}
+
+// The launch shapes of the problem (the autotuner). tune = 1: once per problem
+// shape and process, at the first step, both shapes are timed on the caller's
+// stream (which this synchronizes): the projector on the state's u into the
+// residual buffer, and the backprojector's store form from the residual buffer
+// into the transposed-u buffer, each twice after a warm-up launch; the faster
+// shape of each operator is kept and cached. Both buffers are rewritten before
+// they are read again (the residual by the first inner step, u^T by a transpose
+// of u). tune = 0 / 2 keep the wide / narrow shapes set at create.
+static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w, cudaStream_t s) {
+    h.tuned = true;
+    if (h.tune != DADMM_TUNE_AUTO) return;
+    const std::vector<long long> key = shape_key(h);
+    int tile = 0, bins = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        auto it = g_shape_cache.find(key);
+        if (it != g_shape_cache.end()) {
+            tile = it->second.first;
+            bins = it->second.second;
+        }
+    }
+    if (!tile) {
+        const int tile_c[2] = {kBpTileXWide, kBpTileXNarrow};
+        const int bins_c[2] = {kProjItemBins, kProjItemBinsNarrow};
+        float tp[2] = {0.f, 0.f}, tb[2] = {0.f, 0.f};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        TOMO_CUDA(cudaEventCreate(&e0));
+        cudaError_t ce = cudaEventCreate(&e1);
+        if (ce != cudaSuccess) cudaEventDestroy(e0);
+        TOMO_CUDA(ce);
+        try {
+            for (int c = 0; c < 2; ++c) {
+                h.bp_tile_x = tile_c[c];
+                h.proj_bins4 = bins_c[c];
+                build_lists(h);
+                ProjParams pp = proj_params(h, st, sino, w);
+                pp.items = h.d_pitems;
+                pp.n_items = h.n_pitems;
+                pp.counter = w.counters;
+                BpParams bp = bp_params(h, st, w);
+                bp.items = h.d_bitems;
+                bp.n_items = h.n_bitems;
+                bp.counter = w.counters + 1;
+                bp.img = w.uT;
+                bp.beta = 0.f;
+                for (int op = 0; op < 2; ++op) {
+                    auto run = [&]() {
+                        TOMO_CUDA(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), s));
+                        if (op == 0)
+                            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s);
+                        else
+                            launch_backproject_store(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x);
+                    };
+                    run();  // warm-up
+                    TOMO_CUDA(cudaEventRecord(e0, s));
+                    run();
+                    run();
+                    TOMO_CUDA(cudaEventRecord(e1, s));
+                    TOMO_CUDA(cudaEventSynchronize(e1));
+                    TOMO_CUDA(cudaEventElapsedTime(op == 0 ? &tp[c] : &tb[c], e0, e1));
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h.ut_dirty = true;  // the backprojector trials wrote over u^T
+        tile = tb[1] < tb[0] ? tile_c[1] : tile_c[0];
+        bins = tp[1] < tp[0] ? bins_c[1] : bins_c[0];
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        g_shape_cache.emplace(key, std::make_pair(tile, bins));
+    }
+    if (tile != h.bp_tile_x || bins != h.proj_bins4) {
+        h.bp_tile_x = tile;
+        h.proj_bins4 = bins;
+        build_lists(h);
+    }
+}
+
 static void build_held_table(Dadmm& h, int k0, int n_iters, const uint8_t* drop) {
     const int M = h.M, MM = M * M, D = h.D;
     if ((int)h.held.size() != MM || h.held_k != k0) {  // the lossless versions at k0
@@ -1396,6 +1556,7 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
                           make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
         if (maps != (h.has_maps != 0)) h.drop_graphs();
         h.has_maps = maps ? 1 : 0;
+        if (!h.tuned) tune_shapes(h, *st, sino, w, user);
         if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
             launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
             h.ut_u = st->u;

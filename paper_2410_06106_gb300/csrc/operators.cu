@@ -145,10 +145,10 @@ struct BpWin {
     float h;           // 1 / max(|c|, |s|): applied to the staged window unless the line is prescaled
 };
 
-// tile origin (x0, y0), tile extent kBpTileX x kBpTileY: the lowest bin
+// tile origin (x0, y0), tile extent tw x kBpTileY: the lowest bin
 // coordinate over the tile is at the corner picked by the signs of C and S
-__device__ __forceinline__ void bp_tile_angle(BpAngle& r, BpWin& wv, const BpConst& k, int x0, int y0) {
-    const long long j = x0 + (k.C < 0 ? kBpTileX - 1 : 0);
+__device__ __forceinline__ void bp_tile_angle(BpAngle& r, BpWin& wv, const BpConst& k, int x0, int y0, int tw) {
+    const long long j = x0 + (k.C < 0 ? tw - 1 : 0);
     const long long i = y0 + (k.S > 0 ? kBpTileY - 1 : 0);
     const long long lo = j * k.C - i * k.S + k.K;
     const int w0 = (int)(lo >> 40) - 2;
@@ -253,7 +253,8 @@ __global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
 // thread -> (angle slot, bin offset, row group) of an item:
 // na = 4: 4 angles x 128 bins, warp w takes bins 16 (w & 3) .. + 16 of angles
 //         2 (w >> 2) and + 1 (half-warps of adjacent angles read nearly the
-//         same shared words), and the same bins + 64: two rays per thread;
+//         same shared words), and the same bins + 64: two rays per thread
+//         (narrow items: 4 angles x 64 bins, one ray per thread);
 // na = 2: 2 angles x 128 bins, warp w takes bins 16 w .. + 16 of both;
 // na = 1: 128 bins x 2 row groups (threads 128..255 take rows 16..31 of
 //         every chunk; the two partial sums are added at the end).
@@ -273,7 +274,6 @@ __device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& b
     }
 }
 
-constexpr int kProjItemBins = 128;  // bins of an item: every item holds 128 bins of each of its angles
 
 // NR consecutive rows of one ray inside a staged chunk: the two candidate
 // pixels of each row, weighted by the trapezoid (see the file header); the
@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
         int slot, boff, rgrp;
         proj_lane_map(na, tid, slot, boff, rgrp);
         const int b = item.b0 + boff;
-        const int blast = min(item.b0 + kProjItemBins - 1, B - 1);
-        const int bc = min(b, blast);  // rays past the last bin shadow it (their output is dropped)
-        const bool two = na == 4;      // a second ray, 64 bins further
+        const int blast = min(item.b0 + item.nb - 1, B - 1);
+        const int bc = min(b, blast);          // rays past the last bin shadow it (their output is dropped)
+        const bool two = na == 4 && item.nb == 128;  // a second ray, 64 bins further
         const int b2 = b + 64, bc2 = min(b2, blast);
         const ProjAngle A = sa[slot];
         const int colmaj = sa[0].colmaj;
@@ -532,19 +532,6 @@ __device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, i
     }
 }
 
-// Persistent backprojector. A block takes work items from the queue and walks
-// their angles in chunks of 32. Everything a chunk needs arrives by cp.async
-// ahead of use, so no global latency sits between two chunks: while chunk i
-// accumulates, the windows of chunk i + 1, the per-angle constants of chunk
-// i + 2 and the descriptor of the item three items ahead are in flight, and
-// the queue has already been asked for the item after that. An item's
-// epilogue (Algorithm 2 step or store) overlaps the next chunk's copies.
-// 16 x 8 threads; thread (tx, ty) owns the 4 x 8 pixels (x0 + tx + 16 kx,
-// y0 + ty + 8 ky): a half-warp (16 consecutive tx) reads 16 window pairs
-// within 16 consecutive entries, so its 64-bit shared loads never conflict.
-// A pixel's two candidate bins accumulate in the two lanes of one packed FP32
-// pair (one __ffma2_rn per pixel and angle), added together in the epilogue;
-// 32 pixels per thread spread the per-angle setup over more updates.
 // row `row` of the view of x that Algorithm 2 reads for the item's node: the
 // node's own x (consensus variant), else the message-ring plane of the version
 // the node holds of the row's segment (null before any message arrived)
@@ -561,8 +548,24 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ptr));
 }
 
-template <int EPI>
+// Persistent backprojector. A block takes work items from the queue and walks
+// their angles in chunks of 32. Everything a chunk needs arrives by cp.async
+// ahead of use, so no global latency sits between two chunks: while chunk i
+// accumulates, the windows of chunk i + 1, the per-angle constants of chunk
+// i + 2 and the descriptor of the item three items ahead are in flight, and
+// the queue has already been asked for the item after that. An item's
+// epilogue (Algorithm 2 step or store) overlaps the next chunk's copies.
+// 16 x 8 threads; thread (tx, ty) owns the PX x 8 pixels (x0 + tx + 16 kx,
+// y0 + ty + 8 ky) of a (16 PX) x 64 tile (PX = 4: 64 x 64 tiles; PX = 2:
+// 32 x 64 tiles, twice the items for problems with few of them): a half-warp
+// (16 consecutive tx) reads 16 window pairs within 16 consecutive entries, so
+// its 64-bit shared loads never conflict. A pixel's two candidate bins
+// accumulate in the two lanes of one packed FP32 pair (one __ffma2_rn per
+// pixel and angle), added together in the epilogue; 8 PX pixels per thread
+// spread the per-angle setup over more updates.
+template <int EPI, int PX>
 __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
+    constexpr int TX = 16 * PX;  // tile width
     extern __shared__ __align__(16) unsigned char bp_dyn[];
     float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][kBpChunk][kBpWin]
     __shared__ BpConst s_k[kBpChunk];                  // constants of the chunk after next
@@ -590,7 +593,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
     };
     auto setup = [&](const BpItem& it, int a0, int slot) {
         if (tid < min(kBpChunk, it.na - a0)) {
-            bp_tile_angle(s_a[slot][tid], s_w[slot][tid], s_k[tid], it.tx * kBpTileX, it.ty * kBpTileY);
+            bp_tile_angle(s_a[slot][tid], s_w[slot][tid], s_k[tid], it.tx * TX, it.ty * kBpTileY, TX);
             s_w[slot][tid].row = p.sino + ((size_t)it.sinb + s_k[tid].row) * B;
         }
     };
@@ -635,11 +638,11 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         if (p.view.held) held = p.view.held + (size_t)(kiter - *p.view.k_first) * 2 * p.view.M * p.view.M;
     }
 
-    float2 acc2[8][4];
+    float2 acc2[8][PX];
 #pragma unroll
     for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
+        for (int kx = 0; kx < PX; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
 
     for (;;) {
         cp_async_wait<0>();
@@ -688,12 +691,13 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         cp_async_commit();
         if (EPI == EPI_USTEP && a0 + kBpChunk >= cur.na) {
             // the epilogue follows this chunk: bring its rows of u, lambda and the view
-            // of x into L2 now (two 128-byte lines per 64-pixel row; a hint, no data moves
-            // to registers), so that its loads do not wait on DRAM
-            static_assert(kBpThreads == 2 * kBpTileY && kBpTileX == 64, "two threads per tile row");
-            const int row = cur.ty * kBpTileY + (tid >> 1);
-            const int col = cur.tx * kBpTileX + 32 * (tid & 1);
-            if (row < N && col < N) {
+            // of x into L2 now (one 128-byte line per 32 pixels of a row; a hint, no data
+            // moves to registers), so that its loads do not wait on DRAM
+            constexpr int LPR = TX / 32;  // lines per tile row
+            static_assert(kBpThreads >= LPR * kBpTileY, "one thread per line");
+            const int row = cur.ty * kBpTileY + tid / LPR;
+            const int col = cur.tx * TX + 32 * (tid % LPR);
+            if (tid < LPR * kBpTileY && row < N && col < N) {
                 const size_t o = (size_t)cur.img * n + (size_t)row * N + col;
                 prefetch_l2(p.view.u + o);
                 prefetch_l2(p.view.lam + o);
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             for (int ky = 0; ky < 8; ++ky) {
                 const unsigned prow = pb - (unsigned)ky * sy;
 #pragma unroll
-                for (int kx = 0; kx < 4; ++kx) {
+                for (int kx = 0; kx < PX; ++kx) {
                     const unsigned pp = prow + (unsigned)kx * cx;
                     const float F = one_plus_frac25((int)pp);
                     const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
@@ -727,12 +731,12 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         }
 
         if (a0 + kBpChunk >= cur.na) {  // the item's last chunk: epilogue
-            const int x0 = cur.tx * kBpTileX, y0 = cur.ty * kBpTileY;
-            float acc[8][4];
+            const int x0 = cur.tx * TX, y0 = cur.ty * kBpTileY;
+            float acc[8][PX];
 #pragma unroll
             for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 4; ++kx) acc[ky][kx] = acc2[ky][kx].x + acc2[ky][kx].y;
+                for (int kx = 0; kx < PX; ++kx) acc[ky][kx] = acc2[ky][kx].x + acc2[ky][kx].y;
             if (EPI == EPI_STORE) {
                 float* img = p.img + (size_t)cur.img * n;
 #pragma unroll
@@ -740,7 +744,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     const int row = y0 + ty + 8 * ky;
                     if (row >= N) continue;
 #pragma unroll
-                    for (int kx = 0; kx < 4; ++kx) {
+                    for (int kx = 0; kx < PX; ++kx) {
                         const int col = x0 + tx + 16 * kx;
                         if (col >= N) continue;
                         float* o = img + (size_t)row * N + col;
@@ -770,7 +774,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     const float* xr = xrow[ky];
                     float uo[4], lo[4], xo[4];
 #pragma unroll
-                    for (int kx = 0; kx < 4; ++kx) {
+                    for (int kx = 0; kx < PX; ++kx) {
                         const int col = x0 + tx + 16 * kx;
                         const bool ok = col < N;
                         uo[kx] = ok ? ur[col] : 0.f;
@@ -778,7 +782,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                         xo[kx] = (ok && xr) ? __ldg(xr + col) : 0.f;
                     }
 #pragma unroll
-                    for (int kx = 0; kx < 4; ++kx) {
+                    for (int kx = 0; kx < PX; ++kx) {
                         const int col = x0 + tx + 16 * kx;
                         const float g = acc[ky][kx] + V.rho * (uo[kx] - xo[kx]) + lo[kx];
                         acc[ky][kx] = uo[kx] - eta * g;
@@ -787,17 +791,18 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 }
 
                 if (V.uT) {  // the transposed copy read by the projector's steep-ray items
-                    // 64 x 65 floats in this chunk's stage, free once every thread is done with it
+                    // TX x 65 floats in this chunk's stage, free once every thread is done with it
+                    static_assert(kBpTileY == 64 && 64 * 65 * 4 <= kBpStageFloat2 * 8, "transpose tile");
                     float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
                     __syncthreads();
 #pragma unroll
                     for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-                        for (int kx = 0; kx < 4; ++kx) T[(tx + 16 * kx) * 65 + ty + 8 * ky] = acc[ky][kx];
+                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * 65 + ty + 8 * ky] = acc[ky][kx];
                     __syncthreads();
                     float* ut = V.uT + (size_t)cur.img * n;
 #pragma unroll
-                    for (int i = 0; i < kBpTileX * kBpTileY / kBpThreads; ++i) {
+                    for (int i = 0; i < TX * kBpTileY / kBpThreads; ++i) {
                         const int e = tid + i * kBpThreads;
                         const int cc = e >> 6, rr = e & 63;
                         if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
@@ -807,7 +812,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
 #pragma unroll
             for (int ky = 0; ky < 8; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 4; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
+                for (int kx = 0; kx < PX; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
         }
         if (!v1) break;
         j = j1;
@@ -896,35 +901,43 @@ void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
 
 // the window stages (48 KB) and the largest shared carveout, so that four
 // blocks of each epilogue form fit on an SM; set once per process
+template <int EPI, int PX>
+static cudaError_t set_bp_attr() {
+    cudaError_t e = cudaFuncSetAttribute(backproject_kernel<EPI, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(backproject_kernel<EPI, PX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
 static void ensure_bp_attr() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(backproject_kernel<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBpSmem);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(backproject_kernel<EPI_USTEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kBpSmem);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(backproject_kernel<EPI_STORE>,
-                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(backproject_kernel<EPI_USTEP>,
-                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        err = set_bp_attr<EPI_STORE, 4>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 4>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 2>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2>();
     });
     TOMO_CUDA(err);
 }
 
-void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st) {
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x) {
     if (p.n_items == 0) return;
     ensure_bp_attr();
-    backproject_kernel<EPI_STORE><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    if (tile_x == kBpTileXNarrow)
+        backproject_kernel<EPI_STORE, 2><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    else
+        backproject_kernel<EPI_STORE, 4><<<grid, kBpThreads, kBpSmem, st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
-void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st) {
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x) {
     if (p.n_items == 0) return;
     ensure_bp_attr();
-    backproject_kernel<EPI_USTEP><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    if (tile_x == kBpTileXNarrow)
+        backproject_kernel<EPI_USTEP, 2><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    else
+        backproject_kernel<EPI_USTEP, 4><<<grid, kBpThreads, kBpSmem, st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
@@ -943,15 +956,13 @@ int persistent_grid_project() {
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
-int persistent_grid_backproject(bool ustep) {
+int persistent_grid_backproject(bool ustep, int tile_x) {
     int per_sm = 0;
     ensure_bp_attr();
-    if (ustep)
-        TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_USTEP>,
-                                                                kBpThreads, kBpSmem));
-    else
-        TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backproject_kernel<EPI_STORE>,
-                                                                kBpThreads, kBpSmem));
+    const bool nar = tile_x == kBpTileXNarrow;
+    const void* fn = ustep ? (nar ? (const void*)backproject_kernel<EPI_USTEP, 2> : (const void*)backproject_kernel<EPI_USTEP, 4>)
+                           : (nar ? (const void*)backproject_kernel<EPI_STORE, 2> : (const void*)backproject_kernel<EPI_STORE, 4>);
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBpThreads, kBpSmem));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -1019,7 +1030,7 @@ int chunk_extent(const std::vector<HostProj>& As, int b0, int b1, int m0) {
 }  // namespace
 
 void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int ang_begin,
-                      int ang_count, int img, int outb, std::vector<ProjItem>& out) {
+                      int ang_count, int img, int outb, std::vector<ProjItem>& out, int bins4) {
     const int end = ang_begin + ang_count;
     int i = ang_begin;
     while (i < end) {
@@ -1034,7 +1045,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
             // extent check over every bin run and chunk
             std::vector<HostProj> As;
             for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-            const int wb = kProjItemBins;
+            const int wb = na == 4 ? bins4 : kProjItemBins;
             bool ok = true;
             for (int b0 = 0; b0 < g.B && ok; b0 += wb) {
                 const int b1 = std::min(b0 + wb - 1, g.B - 1);
@@ -1057,7 +1068,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
                                            std::to_string(angs[i].angle) + ")");
         std::vector<HostProj> As;
         for (int k = 0; k < na; ++k) As.push_back(host_proj(g, angs[i + k].angle));
-        const int wb = kProjItemBins;
+        const int wb = na == 4 ? bins4 : kProjItemBins;
         for (int b0 = 0; b0 < g.B; b0 += wb) {
             const int b1 = std::min(b0 + wb - 1, g.B - 1);
             int lo = g.N, hi = -1;
@@ -1077,6 +1088,7 @@ void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int an
             it.b0 = b0;
             it.m_lo = hi >= lo ? lo : 0;
             it.nchunks = hi >= lo ? ceil_div(hi - lo + 1, kProjRows) : 0;
+            it.nb = wb;
             out.push_back(it);
         }
         i += na;
@@ -1093,8 +1105,8 @@ std::vector<BpConst> bp_list_consts(const Geometry& g, const std::vector<AngRow>
 }
 
 void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb, int node,
-                    int slice, std::vector<BpItem>& out) {
-    const int ntx = ceil_div(g.N, kBpTileX), nty = ceil_div(g.N, kBpTileY);
+                    int slice, std::vector<BpItem>& out, int tile_x) {
+    const int ntx = ceil_div(g.N, tile_x), nty = ceil_div(g.N, kBpTileY);
     for (int ty = 0; ty < nty; ++ty)
         for (int tx = 0; tx < ntx; ++tx) {
             BpItem it{};

@@ -83,7 +83,7 @@ struct ProjItem {
     int b0;       // first bin
     int m_lo;     // first major index
     int nchunks;  // chunks of kProjRows major indices
-    int pad;
+    int nb;       // bins of each angle (kProjItemBins, or kProjItemBinsNarrow for 4 narrow angles)
 };
 
 // backprojector work item: one 64 x 64 pixel tile of one image, all the
@@ -105,7 +105,10 @@ constexpr int kProjMaxNa = 4;
 constexpr int kProjStageFloats = kProjRows * kProjPitch;  // one 32 KB stage; two stages in flight
 
 constexpr int kBpThreads = 128;
-constexpr int kBpTileX = 64, kBpTileY = 64;
+constexpr int kBpTileY = 64;  // tile height; the width is 64 (wide) or 32 (narrow)
+constexpr int kBpTileXWide = 64, kBpTileXNarrow = 32;
+constexpr int kProjItemBins = 128;     // bins of each angle of a projector item
+constexpr int kProjItemBinsNarrow = 64;  // 4-angle items of the narrow shape
 constexpr int kBpChunk = 32;  // angles staged per pass
 constexpr int kBpWin = 96;    // window pairs per angle: 63 (|c| + |s|) + 6 < 96
 
@@ -177,10 +180,14 @@ inline bool rows_major(double c, double s) { return std::abs(c) >= std::abs(s); 
 std::vector<BpConst> bp_list_consts(const Geometry& g, const std::vector<AngRow>& angs);
 
 // host builders of work lists (operators.cu)
+// bins4: bins per angle of 4-angle projector items (kProjItemBins or
+// kProjItemBinsNarrow); tile_x: backprojector tile width (kBpTileXWide or
+// kBpTileXNarrow)
 void build_proj_items(const Geometry& g, const std::vector<AngRow>& angs, int ang_begin,
-                      int ang_count, int img, int outb, std::vector<ProjItem>& out);
+                      int ang_count, int img, int outb, std::vector<ProjItem>& out,
+                      int bins4 = kProjItemBins);
 void build_bp_items(const Geometry& g, int ang_begin, int ang_count, int img, int sinb,
-                    int node, int slice, std::vector<BpItem>& out);
+                    int node, int slice, std::vector<BpItem>& out, int tile_x = kBpTileXWide);
 
 // launch parameters. map / mapT: TMA descriptors of the images [nimg][N][N]
 // and of their transposes; items of steep rays (columns major) read mapT,
@@ -240,10 +247,10 @@ struct BpParams {
 
 void launch_project(const ProjParams& p, int grid, cudaStream_t st);
 void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st);
-void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st);
-void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st);
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide);
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide);
 int persistent_grid_project();
-int persistent_grid_backproject(bool ustep);
+int persistent_grid_backproject(bool ustep, int tile_x = kBpTileXWide);
 
 Geometry* as_geometry(tomo_geometry_t g);
 void check_device(const Geometry& g);

@@ -155,6 +155,45 @@ def test_batched_and_plain_forms_are_bit_identical(quant):
     assert np.array_equal(sa, sb)
 
 
+@pytest.mark.parametrize("tune,shape", [("wide", (64, 128)), ("narrow", (32, 64))])
+def test_launch_shapes_follow_the_oracle(tune, shape):
+    """both launch shapes of the operators (64 x 64 backprojector tiles with
+    128-bin projector items; 32 x 64 tiles with 64-bin items for runs of 4
+    angles) by state injection; N = 96 leaves ragged tiles in both"""
+    need_gpu()
+    p = small_problem(N=96, A=64, B=139, M=4, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
+    eta = oracle_eta1(p)
+    s = api.DADMM(p, eta, tune=tune)
+    assert s.launch_shape() == shape
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s.step(sino, 2)
+    before = gpu_state(s)
+    s.step(sino, 1)
+    o = O.DADMM(p, eta)
+    o.load_state(*before)
+    o.iterate(p["sino"])
+    compare_states(gpu_state(s), o, p)
+    assert s.launch_shape() == shape
+
+
+def test_autotuned_shape_is_shared_by_the_solvers_of_a_problem():
+    """the first step of an auto-tuned solver times both shapes and caches the
+    choice for the problem: a second solver, plain or batched, runs the same
+    shapes, so the two forms stay bit-identical"""
+    need_gpu()
+    p = small_problem(N=64, A=40, B=93, M=4, graph="complete", quant="kmeans", noise=0.02, seed=13, km_k=8)
+    eta = oracle_eta1(p)
+    a, b = api.DADMM(p, eta, mode="batched"), api.DADMM(p, eta, mode="plain")
+    sino = torch.as_tensor(p["sino"]).cuda()
+    assert a.launch_shape() == (64, 128)  # until the first step
+    a.step(sino, 3)
+    b.step(sino, 3)
+    assert a.launch_shape() == b.launch_shape()
+    assert a.launch_shape()[0] in (32, 64) and a.launch_shape()[1] in (64, 128)
+    for name in ("u", "lam", "xseg", "hist", "iter"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+
+
 def test_alternating_input_buffers():
     """a caller that alternates input buffers (double-buffered host copies)
     gets the same iterates as one that passes one buffer: each buffer keeps
