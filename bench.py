@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-nodes", type=int, default=64, help="oracle sample: nodes of slice 0")
     ap.add_argument("--ref-nodes", type=int, default=8, help="reference arm: nodes of slice 0 per step")
     ap.add_argument("--slices", type=int, default=None, help="override the number of slices")
+    ap.add_argument("--tune", choices=["auto", "wide", "narrow"], default="auto",
+                    help="launch shapes of the operators (auto: timed at the first step)")
     ap.add_argument("--quick-eta", action="store_true",
                     help="step sizes from the bound ||P_m||^2 <= 1.2 A_m N instead of power iterations")
     return ap.parse_args()
@@ -271,7 +273,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(dev)
 
     with torch.cuda.stream(stream):
-        s = api.DADMM(prob, eta1, mode="batched", geometry=geo)
+        s = api.DADMM(prob, eta1, mode="batched", geometry=geo, tune=args.tune)
         # CUDA events inside the captured graph around every phase; read once after the timed
         # region (the last timed iteration's kernel durations), so no host sync per step
         s.set_profiling(True)
@@ -319,7 +321,7 @@ def run_ours(args, ws, rank, local):
     plain = None
     if not args.no_plain:
         with torch.cuda.stream(stream):
-            p = api.DADMM(prob, eta1, mode="plain", geometry=geo)
+            p = api.DADMM(prob, eta1, mode="plain", geometry=geo, tune=args.tune)
             p.step(sino, 1, stats=False)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -339,7 +341,7 @@ def run_ours(args, ws, rank, local):
         # reconstruction back D2H; the copies run on a second stream, double-buffered,
         # so that step i+1's input and step i's result move while the GPU computes
         with torch.cuda.stream(stream):
-            s = api.DADMM(prob, eta1, mode="batched", geometry=geo)
+            s = api.DADMM(prob, eta1, mode="batched", geometry=geo, tune=args.tune)
             cs = torch.cuda.Stream(dev)
             out_host = [torch.empty(prob["S"], g["N"], g["N"], pin_memory=True) for _ in range(2)]
             d_buf = [torch.empty_like(sino) for _ in range(2)]
@@ -400,7 +402,7 @@ def run_ours(args, ws, rank, local):
                 "data": "synthetic (seeded random-ellipse phantoms, analytic sinograms, 1% noise)",
                 "config": dict(workload_config(args.workload, args.slices), parallelism="replicas" if ws > 1 else "single",
                                mode="batched persistent, graph-captured",
-                               launch_shape={"bp_tile_x": shape[0], "proj_item_bins": shape[1], "tune": "auto"}),
+                               launch_shape={"bp_tile_x": shape[0], "proj_item_bins": shape[1], "tune": args.tune}),
                 "plain": plain, "e2e": e2e,
                 "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_tflops,
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
