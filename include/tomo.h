@@ -18,6 +18,10 @@
  *   library-owned and released by their destroy call.
  * - Work is enqueued asynchronously on `stream` (NULL = legacy default
  *   stream); no call synchronizes unless documented.
+ * - Handles (geometries, solvers) may be used from several host threads
+ *   only one call at a time: the caller serializes calls on one handle.
+ *   Distinct handles are independent (the process-wide cache of autotuned
+ *   launch shapes is locked internally).
  * - Images are float32 [N][N] row-major, pixel (i, j) centred at
  *   x = j - (N-1)/2, y = (N-1)/2 - i (row 0 at the top, y up), unit pixels.
  *   Sinograms are float32 [angles][B] row-major; ray (a, b) is the line
