@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cpu-nodes", type=int, default=64, help="oracle sample: nodes of slice 0")
     ap.add_argument("--ref-nodes", type=int, default=8, help="reference arm: nodes of slice 0 per step")
     ap.add_argument("--slices", type=int, default=None, help="override the number of slices")
-    ap.add_argument("--tune", choices=["auto", "wide", "narrow"], default="auto",
+    ap.add_argument("--tune", choices=["auto", "wide", "narrow", "pairs"], default="auto",
                     help="launch shapes of the operators (auto: timed at the first step)")
     ap.add_argument("--quick-eta", action="store_true",
                     help="step sizes from the bound ||P_m||^2 <= 1.2 A_m N instead of power iterations")
@@ -402,7 +402,8 @@ def run_ours(args, ws, rank, local):
                 "data": "synthetic (seeded random-ellipse phantoms, analytic sinograms, 1% noise)",
                 "config": dict(workload_config(args.workload, args.slices), parallelism="replicas" if ws > 1 else "single",
                                mode="batched persistent, graph-captured",
-                               launch_shape={"bp_tile_x": shape[0], "proj_item_bins": shape[1], "tune": args.tune}),
+                               launch_shape={"bp_tile_x": shape[0], "bp_slices": shape[1], "proj_item_bins": shape[2],
+                                             "tune": args.tune}),
                 "plain": plain, "e2e": e2e,
                 "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_tflops,
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,

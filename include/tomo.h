@@ -274,14 +274,17 @@ typedef struct {
     int max_stale; /* >= 0: extra iterations a held message may age through losses
                       (dadmm_step_lossy); deepens the message ring by as many planes */
     int variant;   /* DADMM_VARIANT_SEGMENTS (Algorithm 4) or DADMM_VARIANT_CONSENSUS */
-    int tune;      /* launch shapes: DADMM_TUNE_WIDE, DADMM_TUNE_AUTO or DADMM_TUNE_NARROW */
+    int tune;      /* launch shapes: DADMM_TUNE_WIDE, _AUTO, _NARROW or _PAIRS */
 } dadmm_config;
 
 /* Launch shapes of the two operators. Wide: 64 x 64-pixel backprojector tiles
  * and 128-bin projector items; narrow: 32 x 64 tiles and 64-bin items for
  * runs of 4 angles (twice the work items, for problems with few of them).
- * Auto: the first dadmm_step of the solver times both shapes of each operator
- * on its own state and keeps the faster (synchronizing the stream once; do not
+ * With an even number of slices, the batched backprojector may also take
+ * slice-pair items (narrow tiles, two slices per item sharing positions and
+ * weights); the plain form then runs single-slice narrow tiles, with identical
+ * results. Auto: the first dadmm_step of the solver times the shapes of each
+ * operator on its own state and keeps the fastest (synchronizing the stream once; do not
  * make that first call while the stream is being captured); the choice is
  * cached per device and problem shape for the life of the process, so solvers
  * of the same problem, batched or plain, run the same shapes. Results differ
@@ -290,6 +293,9 @@ typedef struct {
 #define DADMM_TUNE_WIDE 0
 #define DADMM_TUNE_AUTO 1
 #define DADMM_TUNE_NARROW 2
+/* narrow shapes with slice-pair backprojector items in the batched form
+ * (needs an even S) */
+#define DADMM_TUNE_PAIRS 3
 
 /* Algorithm 4: every node owns a segment of x and the segments travel over the
  * graph (the paper's decentralized ADMM). */
@@ -317,10 +323,12 @@ TOMO_API tomo_status dadmm_destroy(dadmm_t h);
 /* Depth D of the message ring (maximum hop distance + 1). */
 TOMO_API int dadmm_ring_depth(dadmm_t h);
 
-/* The launch shapes in use: backprojector tile width in pixels (64 or 32) and
+/* The launch shapes in use: backprojector tile width in pixels (64 or 32),
+ * slices per batched backprojector item (1, or 2: two slices of one node and
+ * tile share the position and weight arithmetic; narrow tiles, even S), and
  * bins per angle of 4-angle projector items (128 or 64). With
  * DADMM_TUNE_AUTO these are the wide shapes until the first dadmm_step. */
-TOMO_API tomo_status dadmm_launch_shape(dadmm_t h, int* bp_tile_x, int* proj_item_bins);
+TOMO_API tomo_status dadmm_launch_shape(dadmm_t h, int* bp_tile_x, int* bp_slices, int* proj_item_bins);
 
 /* Device state, all caller-owned float32 unless noted:
  *   u, lam  [S][M][N][N]    local images u_m and duals lambda_m

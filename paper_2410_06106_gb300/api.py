@@ -74,7 +74,7 @@ SIGNATURES = {
     "dadmm_create": (C.c_int, [C.c_void_p, C.POINTER(DadmmConfig), C.c_void_p]),
     "dadmm_destroy": (C.c_int, [C.c_void_p]),
     "dadmm_ring_depth": (C.c_int, [C.c_void_p]),
-    "dadmm_launch_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dadmm_launch_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dadmm_state_size": (C.c_size_t, [C.c_void_p]),
     "dadmm_state_init": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p]),
     "dadmm_workspace_size": (C.c_size_t, [C.c_void_p]),
@@ -309,7 +309,8 @@ class DADMM:
 
     def __init__(self, prob, eta1, mode="batched", geometry=None, tune="auto"):
         """tune: launch shapes, "auto" (timed at the first step, cached per
-        problem shape in the process), "wide" or "narrow" (see dadmm_config)"""
+        problem shape in the process), "wide", "narrow" or "pairs" (narrow with
+        slice-pair backprojector items, even S; see dadmm_config)"""
         g = prob["geometry"]
         self.N, self.B, self.A = g["N"], g["B"], g["A"]
         self.S, self.M = int(prob["S"]), int(prob["M"])
@@ -341,9 +342,9 @@ class DADMM:
         if self.variant not in ("segments", "consensus"):
             raise TomoError(-1, "variant must be 'segments' or 'consensus'")
         cfg.variant = 1 if self.variant == "consensus" else 0
-        tunes = {"wide": 0, "auto": 1, "narrow": 2}
+        tunes = {"wide": 0, "auto": 1, "narrow": 2, "pairs": 3}
         if tune not in tunes:
-            raise TomoError(-1, "tune must be 'auto', 'wide' or 'narrow'")
+            raise TomoError(-1, "tune must be 'auto', 'wide', 'narrow' or 'pairs'")
         cfg.tune = tunes[tune]
         self.mode = mode
         self.cfg = cfg
@@ -433,10 +434,11 @@ class DADMM:
         return out
 
     def launch_shape(self):
-        """(backprojector tile width, bins of 4-angle projector items) in use"""
-        tx, nb = C.c_int(), C.c_int()
-        _check(lib().dadmm_launch_shape(self.handle, C.byref(tx), C.byref(nb)))
-        return tx.value, nb.value
+        """(backprojector tile width, slices per batched backprojector item,
+        bins of 4-angle projector items) in use"""
+        tx, sl, nb = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().dadmm_launch_shape(self.handle, C.byref(tx), C.byref(sl), C.byref(nb)))
+        return tx.value, sl.value, nb.value
 
     @property
     def k(self):

@@ -68,6 +68,7 @@ struct Dadmm {
     int32_t* d_recv = nullptr;
     int32_t* d_home = nullptr;
     float* d_eta1 = nullptr;
+    float* d_eta0 = nullptr;  // [M] zeros: the autotuner's u-step trials leave u as it is
     float* d_mx = nullptr;  // [A] max(|cos|, |sin|) per angle: undoes the residual's prescale
     SegTask* d_km = nullptr;
     SegTask* d_jp = nullptr;
@@ -79,6 +80,7 @@ struct Dadmm {
     // tune: 0 wide shapes, 1 timed at the first step and cached per problem shape,
     // 2 narrow shapes
     int tune = 0, bp_tile_x = kBpTileXWide, proj_bins4 = kProjItemBins;
+    int bp_slices = 1;  // batched backprojector items: 1 slice, or 2 slices of one node and tile
     bool tuned = false;
     std::vector<AngRow> angs;           // node-major angle list
     std::vector<int32_t> node_ang_ptr;  // [M + 1]
@@ -646,7 +648,7 @@ static void free_dadmm(Dadmm* h) {
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
     void* ptrs[] = {h->d_angs, h->d_bk, h->d_pitems, h->d_bitems, h->d_pplain, h->d_bplain, h->d_lag, h->d_kind,
                     h->d_seg_of_row, h->d_need, h->d_recv, h->d_home, h->d_eta1, h->d_mx, h->d_km, h->d_jp,
-                    h->d_nb_ptr, h->d_nb};
+                    h->d_nb_ptr, h->d_nb, h->d_eta0};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -681,19 +683,27 @@ static void build_lists(Dadmm& h) {
             }
         }
     // batched order: node-major, as the plain lists, so that the blocks in flight
-    // work on few nodes at a time and each node's image stays in L2
+    // work on few nodes at a time and each node's image stays in L2; with slice
+    // pairs, the items of the even slices, each also covering the next slice
+    std::vector<BpItem> bbatch;
+    if (h.bp_slices == 2) {
+        for (const BpItem& it : bplain)
+            if (it.slice % 2 == 0) bbatch.push_back(it);
+    } else {
+        bbatch = bplain;
+    }
     for (void* q : {(void*)h.d_pitems, (void*)h.d_bitems, (void*)h.d_pplain, (void*)h.d_bplain})
         if (q) cudaFree(q);
     h.d_pitems = h.d_pplain = nullptr;
     h.d_bitems = h.d_bplain = nullptr;
     h.d_pitems = device_upload(pplain);
-    h.d_bitems = device_upload(bplain);
+    h.d_bitems = device_upload(bbatch);
     h.d_pplain = device_upload(pplain);
     h.d_bplain = device_upload(bplain);
     h.n_pitems = (int)pplain.size();
-    h.n_bitems = (int)bplain.size();
+    h.n_bitems = (int)bbatch.size();
     h.grid_proj = persistent_grid_project();
-    h.grid_bp = persistent_grid_backproject(true, h.bp_tile_x);
+    h.grid_bp = persistent_grid_backproject(true, h.bp_tile_x, h.bp_slices);
     h.drop_graphs();
 }
 
@@ -789,6 +799,8 @@ static BpParams bp_params(const Dadmm& h, const dadmm_state& st, const WsPtrs& w
     bp.N = h.N;
     bp.B = h.B;
     bp.prescaled = 1;
+    bp.pair_img = h.M;  // slice-pair items: the next slice's image of the node
+    bp.pair_rows = h.A;  // ... and its residual lines
     bp.view.hist = st.hist;
     bp.view.iter = st.iter;
     bp.view.lag = h.d_lag;
@@ -842,7 +854,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
             bp.items = h.d_bitems;
             bp.n_items = h.n_bitems;
             bp.counter = w.counters + 2 * e + 1;
-            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x);
+            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x, h.bp_slices);
         } else {
             mark();
             for (int sn = 0; sn < h.S * h.M; ++sn) {
@@ -1191,10 +1203,13 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->node_ang_ptr.assign(c.node_ang_ptr, c.node_ang_ptr + M + 1);
             h->d_angs = device_upload(angs);
             h->d_bk = device_upload(bp_list_consts(*g, angs));
-            TOMO_REQUIRE(c.tune == DADMM_TUNE_WIDE || c.tune == DADMM_TUNE_AUTO || c.tune == DADMM_TUNE_NARROW,
+            TOMO_REQUIRE(c.tune == DADMM_TUNE_WIDE || c.tune == DADMM_TUNE_AUTO || c.tune == DADMM_TUNE_NARROW ||
+                             c.tune == DADMM_TUNE_PAIRS,
                          "unknown tune setting");
+            TOMO_REQUIRE(c.tune != DADMM_TUNE_PAIRS || c.S % 2 == 0, "slice pairs need an even number of slices");
             h->tune = c.tune;
-            if (c.tune == DADMM_TUNE_NARROW) {
+            if (c.tune == DADMM_TUNE_PAIRS) h->bp_slices = 2;
+            if (c.tune == DADMM_TUNE_NARROW || c.tune == DADMM_TUNE_PAIRS) {
                 h->bp_tile_x = kBpTileXNarrow;
                 h->proj_bins4 = kProjItemBinsNarrow;
             }
@@ -1214,6 +1229,7 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             std::vector<float> eta(M);
             for (int m = 0; m < M; ++m) eta[m] = (float)c.eta1[m];
             h->d_eta1 = device_upload(eta);
+            h->d_eta0 = device_upload(std::vector<float>(M, 0.f));
             std::vector<float> mx(g->A);
             for (int a = 0; a < g->A; ++a) mx[a] = (float)std::fmax(std::fabs(g->c[a]), std::fabs(g->s[a]));
             h->d_mx = device_upload(mx);
@@ -1292,11 +1308,12 @@ tomo_status dadmm_destroy(dadmm_t hh) {
 
 int dadmm_ring_depth(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->D : 0; }
 
-tomo_status dadmm_launch_shape(dadmm_t hh, int* bp_tile_x, int* proj_item_bins) {
+tomo_status dadmm_launch_shape(dadmm_t hh, int* bp_tile_x, int* bp_slices, int* proj_item_bins) {
     return guard([&] {
         Dadmm& h = *as_dadmm(hh);
-        TOMO_REQUIRE(bp_tile_x && proj_item_bins, "output pointers must be non-NULL");
+        TOMO_REQUIRE(bp_tile_x && bp_slices && proj_item_bins, "output pointers must be non-NULL");
         *bp_tile_x = h.bp_tile_x;
+        *bp_slices = h.bp_slices;
         *proj_item_bins = h.proj_bins4;
     });
 }
@@ -1371,7 +1388,11 @@ namespace tomo {
 // process-wide choices of the launch shapes, keyed by the device and the
 // problem's shape (sizes, trig table, angle partition)
 static std::mutex g_shape_mu;
-static std::map<std::vector<long long>, std::pair<int, int>> g_shape_cache;
+// launch shapes: backprojector tile width and slices per item, projector item bins
+struct Shape {
+    int tile_x, slices, bins4;
+};
+static std::map<std::vector<long long>, Shape> g_shape_cache;
 
 static std::vector<long long> shape_key(const Dadmm& h) {
     int dev = 0;
@@ -1398,39 +1419,42 @@ static std::vector<long long> shape_key(const Dadmm& h) {
 }
 
 // The launch shapes of the problem (the autotuner). tune = 1: once per problem
-// shape and process, at the first step, both shapes are timed on the caller's
-// stream (which this synchronizes): the projector on the state's u into the
-// residual buffer, and the backprojector's store form from the residual buffer
-// into the transposed-u buffer, each twice after a warm-up launch; the faster
-// shape of each operator is kept and cached. Both buffers are rewritten before
-// they are read again (the residual by the first inner step, u^T by a transpose
-// of u). tune = 0 / 2 keep the wide / narrow shapes set at create.
+// shape and process, at the first step, the candidate shapes are timed on the
+// caller's stream (which this synchronizes): the projector's item widths on the
+// state's u into the residual buffer, then the backprojector's tiles (wide,
+// narrow, and narrow slice pairs when S is even) as the Algorithm 2 step itself
+// with every step size eta1 = 0, so that u is rewritten with its own values
+// (and u^T with their transpose); each twice after a warm-up launch. The
+// fastest shape of each operator is kept and cached. The residual buffer is
+// rewritten by the first inner step before it is read again. tune = 0 / 2 / 3
+// keep the wide / narrow / slice-pair shapes set at create.
 static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w, cudaStream_t s) {
     h.tuned = true;
     if (h.tune != DADMM_TUNE_AUTO) return;
     const std::vector<long long> key = shape_key(h);
-    int tile = 0, bins = 0;
+    Shape pick{0, 0, 0};
     {
         std::lock_guard<std::mutex> lk(g_shape_mu);
         auto it = g_shape_cache.find(key);
-        if (it != g_shape_cache.end()) {
-            tile = it->second.first;
-            bins = it->second.second;
-        }
+        if (it != g_shape_cache.end()) pick = it->second;
     }
-    if (!tile) {
-        const int tile_c[2] = {kBpTileXWide, kBpTileXNarrow};
+    if (!pick.tile_x) {
+        // candidates: projector item widths x backprojector tiles (timed separately)
         const int bins_c[2] = {kProjItemBins, kProjItemBinsNarrow};
-        float tp[2] = {0.f, 0.f}, tb[2] = {0.f, 0.f};
+        std::vector<std::pair<int, int>> bp_c = {{kBpTileXWide, 1}, {kBpTileXNarrow, 1}};
+        if (h.S % 2 == 0) bp_c.push_back({kBpTileXNarrow, 2});
+        const int nc = std::max<int>(2, (int)bp_c.size());
+        std::vector<float> tp(nc, INFINITY), tb(nc, INFINITY);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         TOMO_CUDA(cudaEventCreate(&e0));
         cudaError_t ce = cudaEventCreate(&e1);
         if (ce != cudaSuccess) cudaEventDestroy(e0);
         TOMO_CUDA(ce);
         try {
-            for (int c = 0; c < 2; ++c) {
-                h.bp_tile_x = tile_c[c];
-                h.proj_bins4 = bins_c[c];
+            for (int c = 0; c < nc; ++c) {
+                h.proj_bins4 = bins_c[std::min(c, 1)];
+                h.bp_tile_x = bp_c[std::min<size_t>(c, bp_c.size() - 1)].first;
+                h.bp_slices = bp_c[std::min<size_t>(c, bp_c.size() - 1)].second;
                 build_lists(h);
                 ProjParams pp = proj_params(h, st, sino, w);
                 pp.items = h.d_pitems;
@@ -1440,15 +1464,17 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
                 bp.items = h.d_bitems;
                 bp.n_items = h.n_bitems;
                 bp.counter = w.counters + 1;
-                bp.img = w.uT;
-                bp.beta = 0.f;
+                bp.view.eta1 = h.d_eta0;
                 for (int op = 0; op < 2; ++op) {
+                    if (op == 0 && c >= 2) continue;  // two projector candidates
+                    if (op == 1 && c >= (int)bp_c.size()) continue;
                     auto run = [&]() {
                         TOMO_CUDA(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), s));
                         if (op == 0)
                             launch_project(pp, std::min(h.grid_proj, h.n_pitems), s);
                         else
-                            launch_backproject_store(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x);
+                            launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x,
+                                                     h.bp_slices);
                     };
                     run();  // warm-up
                     TOMO_CUDA(cudaEventRecord(e0, s));
@@ -1466,15 +1492,18 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        h.ut_dirty = true;  // the backprojector trials wrote over u^T
-        tile = tb[1] < tb[0] ? tile_c[1] : tile_c[0];
-        bins = tp[1] < tp[0] ? bins_c[1] : bins_c[0];
+        h.ut_dirty = true;  // u^T is rebuilt from u before the first iteration reads it
+        const int bi = (int)(std::min_element(tb.begin(), tb.begin() + bp_c.size()) - tb.begin());
+        pick.tile_x = bp_c[bi].first;
+        pick.slices = bp_c[bi].second;
+        pick.bins4 = tp[1] < tp[0] ? bins_c[1] : bins_c[0];
         std::lock_guard<std::mutex> lk(g_shape_mu);
-        g_shape_cache.emplace(key, std::make_pair(tile, bins));
+        g_shape_cache.emplace(key, pick);
     }
-    if (tile != h.bp_tile_x || bins != h.proj_bins4) {
-        h.bp_tile_x = tile;
-        h.proj_bins4 = bins;
+    if (pick.tile_x != h.bp_tile_x || pick.slices != h.bp_slices || pick.bins4 != h.proj_bins4) {
+        h.bp_tile_x = pick.tile_x;
+        h.bp_slices = pick.slices;
+        h.proj_bins4 = pick.bins4;
         build_lists(h);
     }
 }
@@ -1556,13 +1585,17 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
                           make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
         if (maps != (h.has_maps != 0)) h.drop_graphs();
         h.has_maps = maps ? 1 : 0;
+        auto refresh_ut = [&]() {
+            if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
+                launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
+                h.ut_u = st->u;
+                h.ut_ws = workspace;
+                h.ut_dirty = false;
+            }
+        };
+        refresh_ut();  // the autotuner's projector trials read u^T too
         if (!h.tuned) tune_shapes(h, *st, sino, w, user);
-        if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
-            launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
-            h.ut_u = st->u;
-            h.ut_ws = workspace;
-            h.ut_dirty = false;
-        }
+        refresh_ut();
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,
                                                   w.resid, (const void*)(uintptr_t)(h.lossy ? 1 : 0)};

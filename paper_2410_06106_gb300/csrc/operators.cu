@@ -515,13 +515,18 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // asynchronous copies of a chunk's windows: win[a][k] = (r[w0 + k], r[w0 + k + 1])
 // of the line, zero outside [0, B); warp w takes angles w, w + 8, ...
-__device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, int nac, int B, int tid) {
+// the windows of a chunk's nac angles for SL slices: slice s's window of angle
+// a at win + (s CH + a) kBpWin, its line `row_step` floats after slice 0's
+template <int SL, int CH, int NT>
+__device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, int nac, int B, size_t row_step,
+                                                 int tid) {
     static_assert(kBpWin == 96, "three pairs per lane");
     const int lane = tid & 31;
-    for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
+    for (int e = tid >> 5; e < SL * nac; e += NT / 32) {
+        const int sl = SL == 1 ? 0 : e / nac, a = SL == 1 ? e : e - sl * nac;
         const int w0 = wv[a].w0;
-        const float* row = wv[a].row;
-        float* d = reinterpret_cast<float*>(win + a * kBpWin);
+        const float* row = wv[a].row + sl * row_step;
+        float* d = reinterpret_cast<float*>(win + (sl * CH + a) * kBpWin);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const int k = lane + 32 * q, b = w0 + k;
@@ -563,14 +568,24 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
 // accumulate in the two lanes of one packed FP32 pair (one __ffma2_rn per
 // pixel and angle), added together in the epilogue; 8 PX pixels per thread
 // spread the per-angle setup over more updates.
-template <int EPI, int PX>
-__global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpParams p) {
-    constexpr int TX = 16 * PX;  // tile width
+// threads of a block: 16 x 8, or 16 x 16 for slice pairs (more warps to cover
+// their shorter chunks); RPT rows of pixels per thread
+__host__ __device__ constexpr int bp_threads(int slices) { return slices == 2 ? 256 : kBpThreads; }
+
+template <int EPI, int PX, int SL>
+__global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? 3 : 4) backproject_kernel(const BpParams p) {
+    constexpr int NT = bp_threads(SL);
+    constexpr int TY = NT / 16;          // thread rows
+    constexpr int RPT = kBpTileY / TY;   // pixel rows per thread (8, or 4 for slice pairs)
+    constexpr int TX = 16 * PX;          // tile width
+    constexpr int CH = kBpChunk / SL;    // angles per chunk: a stage holds SL windows per angle
+    static_assert(SL == 1 || PX == 2, "slice pairs use the narrow tiles (registers)");
     extern __shared__ __align__(16) unsigned char bp_dyn[];
-    float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][kBpChunk][kBpWin]
-    __shared__ BpConst s_k[kBpChunk];                  // constants of the chunk after next
-    __shared__ BpAngle s_a[2][kBpChunk];               // this chunk and the next, for their tiles
-    __shared__ BpWin s_w[2][kBpChunk];
+    float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][SL][CH][kBpWin]
+    __shared__ BpConst s_k[CH];                        // constants of the chunk after next
+    __shared__ BpAngle s_a[2][CH];                     // this chunk and the next, for their tiles
+    __shared__ BpWin s_w[2][CH];
+    const size_t row_step = (size_t)p.pair_rows * p.B;  // second slice's sinogram lines
     __shared__ BpItem s_d[4];                          // descriptors of the block's items j .. j + 3
     __shared__ int s_idx[4];                           // their queue indices (>= n_items: none)
     const int tid = threadIdx.x;
@@ -586,13 +601,13 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                        reinterpret_cast<const float*>(p.items + idx) + 4 * tid);
     };
     auto issue_consts = [&](const BpItem& it, int a0) {
-        const int nac = min(kBpChunk, it.na - a0);
+        const int nac = min(CH, it.na - a0);
         if (tid < 4 * nac)
             cp_async16(reinterpret_cast<float*>(&s_k[tid >> 2]) + 4 * (tid & 3),
                        reinterpret_cast<const float*>(p.bk + it.ang0 + a0 + (tid >> 2)) + 4 * (tid & 3));
     };
     auto setup = [&](const BpItem& it, int a0, int slot) {
-        if (tid < min(kBpChunk, it.na - a0)) {
+        if (tid < min(CH, it.na - a0)) {
             bp_tile_angle(s_a[slot][tid], s_w[slot][tid], s_k[tid], it.tx * TX, it.ty * kBpTileY, TX);
             s_w[slot][tid].row = p.sino + ((size_t)it.sinb + s_k[tid].row) * B;
         }
@@ -626,8 +641,8 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
     int j = 0, a0 = 0, buf = 0;  // the current chunk: item ordinal j, first angle a0
     {
         const BpItem it = s_d[0];
-        bp_issue_windows(wins, s_w[0], min(kBpChunk, it.na), B, tid);
-        if (kBpChunk < it.na) issue_consts(it, kBpChunk);
+        bp_issue_windows<SL, CH, NT>(wins, s_w[0], min(CH, it.na), B, row_step, tid);
+        if (CH < it.na) issue_consts(it, CH);
         else if (s_idx[1] < n_items) issue_consts(s_d[1], 0);
         cp_async_commit();
     }
@@ -638,35 +653,38 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         if (p.view.held) held = p.view.held + (size_t)(kiter - *p.view.k_first) * 2 * p.view.M * p.view.M;
     }
 
-    float2 acc2[8][PX];
+    float2 acc2[SL][RPT][PX];
 #pragma unroll
-    for (int ky = 0; ky < 8; ++ky)
+    for (int sl = 0; sl < SL; ++sl)
 #pragma unroll
-        for (int kx = 0; kx < PX; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
+        for (int ky = 0; ky < RPT; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < PX; ++kx) acc2[sl][ky][kx] = make_float2(0.f, 0.f);
 
     for (;;) {
         cp_async_wait<0>();
         __syncthreads();  // (A) windows of this chunk, constants of the next, descriptors up to j + 2 landed
         const BpItem cur = s_d[j & 3];
-        const int nac = min(kBpChunk, cur.na - a0);
+        const int nac = min(CH, cur.na - a0);
         // the next two chunks of the stream
-        int j1 = j, a1 = a0 + kBpChunk;
+        int j1 = j, a1 = a0 + CH;
         if (a1 >= cur.na) {
             j1 = j + 1;
             a1 = 0;
         }
         const bool v1 = s_idx[j1 & 3] < n_items;
         const BpItem it1 = s_d[j1 & 3];
-        int j2 = j1, a2 = a1 + kBpChunk;
+        int j2 = j1, a2 = a1 + CH;
         if (v1 && a2 >= it1.na) {
             j2 = j1 + 1;
             a2 = 0;
         }
         const bool v2 = v1 && s_idx[j2 & 3] < n_items;
         if (!p.prescaled) {  // fold h into the pairs this thread copied (its own copies have landed)
-            for (int a = tid >> 5; a < nac; a += kBpThreads / 32) {
+            for (int e = tid >> 5; e < SL * nac; e += NT / 32) {
+                const int sl = SL == 1 ? 0 : e / nac, a = SL == 1 ? e : e - sl * nac;
                 const float h = s_w[buf][a].h;
-                float2* w = wins + buf * kBpStageFloat2 + a * kBpWin;
+                float2* w = wins + buf * kBpStageFloat2 + (sl * CH + a) * kBpWin;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const float2 v = w[(tid & 31) + 32 * q];
@@ -676,7 +694,7 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
         }
         if (v1) setup(it1, a1, buf ^ 1);
         __syncthreads();  // (B) the next chunk's angles are set; the constants slot is free
-        if (v1) bp_issue_windows(wins + (buf ^ 1) * kBpStageFloat2, s_w[buf ^ 1], min(kBpChunk, it1.na - a1), B, tid);
+        if (v1) bp_issue_windows<SL, CH, NT>(wins + (buf ^ 1) * kBpStageFloat2, s_w[buf ^ 1], min(CH, it1.na - a1), B, row_step, tid);
         if (v2) issue_consts(s_d[j2 & 3], a2);
         if (a0 == 0 && tid < 32) {  // a new item: the descriptor three items ahead, one more queue index
             const int slot = (j + 3) & 3;
@@ -689,19 +707,23 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             issue_desc(slot, __shfl_sync(0xffffffffu, idx, 0));
         }
         cp_async_commit();
-        if (EPI == EPI_USTEP && a0 + kBpChunk >= cur.na) {
+        if (EPI == EPI_USTEP && a0 + CH >= cur.na) {
             // the epilogue follows this chunk: bring its rows of u, lambda and the view
             // of x into L2 now (one 128-byte line per 32 pixels of a row; a hint, no data
             // moves to registers), so that its loads do not wait on DRAM
             constexpr int LPR = TX / 32;  // lines per tile row
-            static_assert(kBpThreads >= LPR * kBpTileY, "one thread per line");
-            const int row = cur.ty * kBpTileY + tid / LPR;
-            const int col = cur.tx * TX + 32 * (tid % LPR);
-            if (tid < LPR * kBpTileY && row < N && col < N) {
-                const size_t o = (size_t)cur.img * n + (size_t)row * N + col;
+            static_assert(NT >= SL * LPR * kBpTileY, "one thread per line");
+            const int sl = tid / (LPR * kBpTileY), t = tid - sl * (LPR * kBpTileY);
+            const int row = cur.ty * kBpTileY + t / LPR;
+            const int col = cur.tx * TX + 32 * (t % LPR);
+            if (tid < SL * LPR * kBpTileY && row < N && col < N) {
+                BpItem cs = cur;
+                cs.img += sl * p.pair_img;
+                cs.slice += sl;
+                const size_t o = (size_t)cs.img * n + (size_t)row * N + col;
                 prefetch_l2(p.view.u + o);
                 prefetch_l2(p.view.lam + o);
-                const float* xr = bp_view_row(p.view, cur, row, held, kiter, n, N);
+                const float* xr = bp_view_row(p.view, cs, row, held, kiter, n, N);
                 if (xr) prefetch_l2(xr + col);
             }
         }
@@ -713,35 +735,44 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
             const float2* wa = win + a * kBpWin;
             const float gam = A.gam, wf0 = A.wf0, wf1 = A.wf1;
             // position - w0 of pixel (x0 + tx, y0 + ty), 2^-25 (non-negative in the tile)
-            const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)(ty * A.S25);
-            const unsigned cx = (unsigned)A.CX16, sy = (unsigned)A.SY8;
+            // row ty + TY ky = (ty & 7) + 8 (ty >> 3 + (TY / 8) ky): the same integer positions
+            // (steps of one row and of 8 rows) whatever the block's thread rows
+            const unsigned pb = A.P0 + (unsigned)(tx * A.C25) - (unsigned)((ty & 7) * A.S25) -
+                                (unsigned)((ty >> 3) * A.SY8);
+            const unsigned cx = (unsigned)A.CX16, sy = (unsigned)(TY / 8) * (unsigned)A.SY8;
 #pragma unroll
-            for (int ky = 0; ky < 8; ++ky) {
+            for (int ky = 0; ky < RPT; ++ky) {
                 const unsigned prow = pb - (unsigned)ky * sy;
 #pragma unroll
                 for (int kx = 0; kx < PX; ++kx) {
                     const unsigned pp = prow + (unsigned)kx * cx;
                     const float F = one_plus_frac25((int)pp);
-                    const float2 r = wa[pp >> kFracBits];  // (lower bin, upper bin)
-                    const float w0 = __saturatef(fmaf(-gam, F, wf0));
-                    const float w1 = __saturatef(fmaf(gam, F, wf1));
-                    acc2[ky][kx] = __ffma2_rn(make_float2(w0, w1), r, acc2[ky][kx]);
+                    const float2* rp = wa + (pp >> kFracBits);  // (lower bin, upper bin) of slice 0
+                    const float2 wgt = make_float2(__saturatef(fmaf(-gam, F, wf0)), __saturatef(fmaf(gam, F, wf1)));
+#pragma unroll
+                    for (int sl = 0; sl < SL; ++sl)  // the same position and weights serve every slice
+                        acc2[sl][ky][kx] = __ffma2_rn(wgt, rp[sl * CH * kBpWin], acc2[sl][ky][kx]);
                 }
             }
         }
 
-        if (a0 + kBpChunk >= cur.na) {  // the item's last chunk: epilogue
+        if (a0 + CH >= cur.na) {  // the item's last chunk: epilogue, slice by slice
             const int x0 = cur.tx * TX, y0 = cur.ty * kBpTileY;
-            float acc[8][PX];
 #pragma unroll
-            for (int ky = 0; ky < 8; ++ky)
+            for (int sl = 0; sl < SL; ++sl) {
+            BpItem cs = cur;  // this slice's image and message planes
+            cs.img += sl * p.pair_img;
+            cs.slice += sl;
+            float acc[RPT][PX];
 #pragma unroll
-                for (int kx = 0; kx < PX; ++kx) acc[ky][kx] = acc2[ky][kx].x + acc2[ky][kx].y;
+            for (int ky = 0; ky < RPT; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < PX; ++kx) acc[ky][kx] = acc2[sl][ky][kx].x + acc2[sl][ky][kx].y;
             if (EPI == EPI_STORE) {
-                float* img = p.img + (size_t)cur.img * n;
+                float* img = p.img + (size_t)cs.img * n;
 #pragma unroll
-                for (int ky = 0; ky < 8; ++ky) {
-                    const int row = y0 + ty + 8 * ky;
+                for (int ky = 0; ky < RPT; ++ky) {
+                    const int row = y0 + ty + TY * ky;
                     if (row >= N) continue;
 #pragma unroll
                     for (int kx = 0; kx < PX; ++kx) {
@@ -756,18 +787,18 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                 // Each row's view of x is located first (independent table lookups for
                 // the 4 rows).
                 const BpView& V = p.view;
-                const float eta = V.eta1[cur.node];
-                float* u = V.u + (size_t)cur.img * n;
-                const float* lam = V.lam + (size_t)cur.img * n;
-                const float* xrow[8];
+                const float eta = V.eta1[cs.node];
+                float* u = V.u + (size_t)cs.img * n;
+                const float* lam = V.lam + (size_t)cs.img * n;
+                const float* xrow[RPT];
 #pragma unroll
-                for (int ky = 0; ky < 8; ++ky)
-                    xrow[ky] = bp_view_row(V, cur, min(y0 + ty + 8 * ky, N - 1), held, kiter, n, N);
+                for (int ky = 0; ky < RPT; ++ky)
+                    xrow[ky] = bp_view_row(V, cs, min(y0 + ty + TY * ky, N - 1), held, kiter, n, N);
                 // per row: the 12 loads first, then the updates and stores (a store to u
                 // may alias a later load, so loads are not moved past stores by the compiler)
 #pragma unroll
-                for (int ky = 0; ky < 8; ++ky) {
-                    const int row = y0 + ty + 8 * ky;
+                for (int ky = 0; ky < RPT; ++ky) {
+                    const int row = y0 + ty + TY * ky;
                     if (row >= N) continue;
                     float* ur = u + (size_t)row * N;
                     const float* lr = lam + (size_t)row * N;
@@ -796,23 +827,24 @@ __global__ void __launch_bounds__(kBpThreads, 4) backproject_kernel(const BpPara
                     float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
                     __syncthreads();
 #pragma unroll
-                    for (int ky = 0; ky < 8; ++ky)
+                    for (int ky = 0; ky < RPT; ++ky)
 #pragma unroll
-                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * 65 + ty + 8 * ky] = acc[ky][kx];
+                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * 65 + ty + TY * ky] = acc[ky][kx];
                     __syncthreads();
-                    float* ut = V.uT + (size_t)cur.img * n;
+                    float* ut = V.uT + (size_t)cs.img * n;
 #pragma unroll
-                    for (int i = 0; i < TX * kBpTileY / kBpThreads; ++i) {
-                        const int e = tid + i * kBpThreads;
+                    for (int i = 0; i < TX * kBpTileY / NT; ++i) {
+                        const int e = tid + i * NT;
                         const int cc = e >> 6, rr = e & 63;
                         if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
                     }
                 }
             }
 #pragma unroll
-            for (int ky = 0; ky < 8; ++ky)
+            for (int ky = 0; ky < RPT; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < PX; ++kx) acc2[ky][kx] = make_float2(0.f, 0.f);
+                for (int kx = 0; kx < PX; ++kx) acc2[sl][ky][kx] = make_float2(0.f, 0.f);
+            }
         }
         if (!v1) break;
         j = j1;
@@ -901,11 +933,12 @@ void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
 
 // the window stages (48 KB) and the largest shared carveout, so that four
 // blocks of each epilogue form fit on an SM; set once per process
-template <int EPI, int PX>
+template <int EPI, int PX, int SL>
 static cudaError_t set_bp_attr() {
-    cudaError_t e = cudaFuncSetAttribute(backproject_kernel<EPI, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBpSmem);
+    cudaError_t e = cudaFuncSetAttribute(backproject_kernel<EPI, PX, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kBpSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(backproject_kernel<EPI, PX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(backproject_kernel<EPI, PX, SL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 
@@ -913,32 +946,45 @@ static void ensure_bp_attr() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = set_bp_attr<EPI_STORE, 4>();
-        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 4>();
-        if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 2>();
-        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2>();
+        err = set_bp_attr<EPI_STORE, 4, 1>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 4, 1>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 2, 1>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2, 1>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 2, 2>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2, 2>();
     });
     TOMO_CUDA(err);
 }
 
-void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x) {
+// the instantiation of a launch shape
+template <int EPI>
+static const void* bp_kernel_fn(int tile_x, int slices) {
+    if (slices == 2) return (const void*)backproject_kernel<EPI, 2, 2>;
+    return tile_x == kBpTileXNarrow ? (const void*)backproject_kernel<EPI, 2, 1>
+                                    : (const void*)backproject_kernel<EPI, 4, 1>;
+}
+
+template <int EPI>
+static void launch_bp(const BpParams& p, int grid, cudaStream_t st, int tile_x, int slices) {
     if (p.n_items == 0) return;
     ensure_bp_attr();
-    if (tile_x == kBpTileXNarrow)
-        backproject_kernel<EPI_STORE, 2><<<grid, kBpThreads, kBpSmem, st>>>(p);
-    else
-        backproject_kernel<EPI_STORE, 4><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    if (slices == 2) {
+        if (tile_x != kBpTileXNarrow) fail(TOMO_ERR_INVALID_ARG, "slice pairs need the narrow tiles");
+        backproject_kernel<EPI, 2, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
+    } else if (tile_x == kBpTileXNarrow) {
+        backproject_kernel<EPI, 2, 1><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    } else {
+        backproject_kernel<EPI, 4, 1><<<grid, kBpThreads, kBpSmem, st>>>(p);
+    }
     TOMO_CUDA(cudaGetLastError());
 }
 
-void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x) {
-    if (p.n_items == 0) return;
-    ensure_bp_attr();
-    if (tile_x == kBpTileXNarrow)
-        backproject_kernel<EPI_USTEP, 2><<<grid, kBpThreads, kBpSmem, st>>>(p);
-    else
-        backproject_kernel<EPI_USTEP, 4><<<grid, kBpThreads, kBpSmem, st>>>(p);
-    TOMO_CUDA(cudaGetLastError());
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x, int slices) {
+    launch_bp<EPI_STORE>(p, grid, st, tile_x, slices);
+}
+
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x, int slices) {
+    launch_bp<EPI_USTEP>(p, grid, st, tile_x, slices);
 }
 
 static int sm_count() {
@@ -956,13 +1002,11 @@ int persistent_grid_project() {
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
-int persistent_grid_backproject(bool ustep, int tile_x) {
+int persistent_grid_backproject(bool ustep, int tile_x, int slices) {
     int per_sm = 0;
     ensure_bp_attr();
-    const bool nar = tile_x == kBpTileXNarrow;
-    const void* fn = ustep ? (nar ? (const void*)backproject_kernel<EPI_USTEP, 2> : (const void*)backproject_kernel<EPI_USTEP, 4>)
-                           : (nar ? (const void*)backproject_kernel<EPI_STORE, 2> : (const void*)backproject_kernel<EPI_STORE, 4>);
-    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBpThreads, kBpSmem));
+    const void* fn = ustep ? bp_kernel_fn<EPI_USTEP>(tile_x, slices) : bp_kernel_fn<EPI_STORE>(tile_x, slices);
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bp_threads(slices), kBpSmem));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 

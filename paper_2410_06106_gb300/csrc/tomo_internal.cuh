@@ -242,15 +242,21 @@ struct BpParams {
     int N, B;
     int prescaled;  // 1: sino lines already carry the factor h_a
     float beta;
+    // slice-pair items (two slices of one node and tile, sharing positions and
+    // weights): the second slice's image index and sinogram line offsets
+    int pair_img, pair_rows;
     BpView view;
 };
 
 void launch_project(const ProjParams& p, int grid, cudaStream_t st);
 void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st);
-void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide);
-void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide);
+// slices: 1, or 2 for slice-pair items (narrow tiles only)
+void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide,
+                              int slices = 1);
+void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide,
+                              int slices = 1);
 int persistent_grid_project();
-int persistent_grid_backproject(bool ustep, int tile_x = kBpTileXWide);
+int persistent_grid_backproject(bool ustep, int tile_x = kBpTileXWide, int slices = 1);
 
 Geometry* as_geometry(tomo_geometry_t g);
 void check_device(const Geometry& g);

@@ -155,13 +155,14 @@ def test_batched_and_plain_forms_are_bit_identical(quant):
     assert np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("tune,shape", [("wide", (64, 128)), ("narrow", (32, 64))])
+@pytest.mark.parametrize("tune,shape", [("wide", (64, 1, 128)), ("narrow", (32, 1, 64)), ("pairs", (32, 2, 64))])
 def test_launch_shapes_follow_the_oracle(tune, shape):
-    """both launch shapes of the operators (64 x 64 backprojector tiles with
+    """every launch shape of the operators (64 x 64 backprojector tiles with
     128-bin projector items; 32 x 64 tiles with 64-bin items for runs of 4
-    angles) by state injection; N = 96 leaves ragged tiles in both"""
+    angles; the same with slice-pair backprojector items) by state injection,
+    on two slices; N = 96 leaves ragged tiles in all"""
     need_gpu()
-    p = small_problem(N=96, A=64, B=139, M=4, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
+    p = small_problem(N=96, A=64, B=139, M=4, S=2, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
     eta = oracle_eta1(p)
     s = api.DADMM(p, eta, tune=tune)
     assert s.launch_shape() == shape
@@ -185,13 +186,32 @@ def test_autotuned_shape_is_shared_by_the_solvers_of_a_problem():
     eta = oracle_eta1(p)
     a, b = api.DADMM(p, eta, mode="batched"), api.DADMM(p, eta, mode="plain")
     sino = torch.as_tensor(p["sino"]).cuda()
-    assert a.launch_shape() == (64, 128)  # until the first step
+    assert a.launch_shape() == (64, 1, 128)  # until the first step
     a.step(sino, 3)
     b.step(sino, 3)
-    assert a.launch_shape() == b.launch_shape()
-    assert a.launch_shape()[0] in (32, 64) and a.launch_shape()[1] in (64, 128)
+    assert a.launch_shape()[0] == b.launch_shape()[0] and a.launch_shape()[2] == b.launch_shape()[2]
+    assert a.launch_shape() in [(x, 1, n) for x in (32, 64) for n in (64, 128)] + [(32, 2, 64), (32, 2, 128)]
     for name in ("u", "lam", "xseg", "hist", "iter"):
         assert torch.equal(getattr(a, name), getattr(b, name)), name
+
+
+def test_slice_pairs_equal_single_slice_tiles_bit_for_bit():
+    """slice-pair backprojector items (two slices of a node and tile sharing the
+    position and weight arithmetic) give the same iterates, bit for bit, as
+    single-slice items of the same tiles: batched pairs against the plain form
+    and against batched single-slice narrow tiles, over four slices"""
+    need_gpu()
+    p = small_problem(N=64, A=48, B=93, M=4, S=4, graph="ring", quant="alternate", noise=0.02, seed=21, km_k=8)
+    eta = oracle_eta1(p)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    runs = [api.DADMM(p, eta, tune="pairs"), api.DADMM(p, eta, tune="pairs", mode="plain"),
+            api.DADMM(p, eta, tune="narrow")]
+    assert runs[0].launch_shape() == (32, 2, 64) and runs[2].launch_shape() == (32, 1, 64)
+    stats = [r.step(sino, 4) for r in runs]
+    for r, st in zip(runs[1:], stats[1:]):
+        for name in ("u", "lam", "xseg", "hist", "iter"):
+            assert torch.equal(getattr(runs[0], name), getattr(r, name)), name
+        assert np.array_equal(stats[0], st)
 
 
 def test_alternating_input_buffers():
