@@ -9,8 +9,10 @@ synthetic random-ellipse data shaped like the stress problem: 8 slices of
 counts (8..60) on a random geometric graph of mean degree 6, K-means (k=32)
 and JPEG (quality 75) messages alternated per edge, E1 = E2 = 10.
 
-A step is one ADMM iteration over all slices and nodes. Inputs (u, lambda,
-history: ~20 GB) are far larger than L2, so no flush is needed between steps.
+A step is one ADMM iteration over all slices and nodes. The state and
+workspace (u, lambda, u^T, message history: ~29 GB) are far larger than L2, so
+no flush is needed between steps. The operators' launch shapes are autotuned
+by the solver's first (untimed) step unless --tune fixes them.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm of this build has no GPU implementation).
