@@ -405,7 +405,7 @@ def run_ours(args, ws, rank, local):
                 "config": dict(workload_config(args.workload, args.slices), parallelism="replicas" if ws > 1 else "single",
                                mode="batched persistent, graph-captured",
                                launch_shape={"bp_tile_x": shape[0], "bp_slices": shape[1], "proj_item_bins": shape[2],
-                                             "tune": args.tune}),
+                                             "proj_slices": shape[3], "tune": args.tune}),
                 "plain": plain, "e2e": e2e,
                 "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_tflops,
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,

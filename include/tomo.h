@@ -280,10 +280,11 @@ typedef struct {
 /* Launch shapes of the two operators. Wide: 64 x 64-pixel backprojector tiles
  * and 128-bin projector items; narrow: 32 x 64 tiles and 64-bin items for
  * runs of 4 angles (twice the work items, for problems with few of them).
- * With an even number of slices, the batched backprojector may also take
- * slice-pair items (narrow tiles, two slices per item sharing positions and
- * weights); the plain form then runs single-slice narrow tiles, with identical
- * results. Auto: the first dadmm_step of the solver times the shapes of each
+ * With an even number of slices, both operators may also take slice-pair
+ * items (two slices of one node per item, sharing the position and weight
+ * arithmetic): the batched backprojector on narrow tiles (the plain form then
+ * runs single-slice narrow tiles, with identical results), and the projector
+ * in both forms (chunks of 16 rows). Auto: the first dadmm_step of the solver times the shapes of each
  * operator on its own state and keeps the fastest (synchronizing the stream once; do not
  * make that first call while the stream is being captured); the choice is
  * cached per device and problem shape for the life of the process, so solvers
@@ -293,7 +294,8 @@ typedef struct {
 #define DADMM_TUNE_WIDE 0
 #define DADMM_TUNE_AUTO 1
 #define DADMM_TUNE_NARROW 2
-/* narrow shapes with slice-pair backprojector items in the batched form
+/* slice pairs: narrow backprojector tiles with slice-pair items in the
+ * batched form, and slice-pair projector items (128 bins) in both forms
  * (needs an even S) */
 #define DADMM_TUNE_PAIRS 3
 
@@ -325,10 +327,13 @@ TOMO_API int dadmm_ring_depth(dadmm_t h);
 
 /* The launch shapes in use: backprojector tile width in pixels (64 or 32),
  * slices per batched backprojector item (1, or 2: two slices of one node and
- * tile share the position and weight arithmetic; narrow tiles, even S), and
- * bins per angle of 4-angle projector items (128 or 64). With
- * DADMM_TUNE_AUTO these are the wide shapes until the first dadmm_step. */
-TOMO_API tomo_status dadmm_launch_shape(dadmm_t h, int* bp_tile_x, int* bp_slices, int* proj_item_bins);
+ * tile share the position and weight arithmetic; narrow tiles, even S), bins
+ * per angle of 4-angle projector items (128 or 64), and slices per projector
+ * item (1, or 2: the rays of two slices of one node share their arithmetic;
+ * both forms, even S). With DADMM_TUNE_AUTO these are the wide single-slice
+ * shapes until the first dadmm_step. */
+TOMO_API tomo_status dadmm_launch_shape(dadmm_t h, int* bp_tile_x, int* bp_slices, int* proj_item_bins,
+                                        int* proj_slices);
 
 /* Device state, all caller-owned float32 unless noted:
  *   u, lam  [S][M][N][N]    local images u_m and duals lambda_m

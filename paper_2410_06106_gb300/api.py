@@ -74,7 +74,7 @@ SIGNATURES = {
     "dadmm_create": (C.c_int, [C.c_void_p, C.POINTER(DadmmConfig), C.c_void_p]),
     "dadmm_destroy": (C.c_int, [C.c_void_p]),
     "dadmm_ring_depth": (C.c_int, [C.c_void_p]),
-    "dadmm_launch_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dadmm_launch_shape": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dadmm_state_size": (C.c_size_t, [C.c_void_p]),
     "dadmm_state_init": (C.c_int, [C.c_void_p, C.POINTER(DadmmState), C.c_void_p]),
     "dadmm_workspace_size": (C.c_size_t, [C.c_void_p]),
@@ -435,10 +435,10 @@ class DADMM:
 
     def launch_shape(self):
         """(backprojector tile width, slices per batched backprojector item,
-        bins of 4-angle projector items) in use"""
-        tx, sl, nb = C.c_int(), C.c_int(), C.c_int()
-        _check(lib().dadmm_launch_shape(self.handle, C.byref(tx), C.byref(sl), C.byref(nb)))
-        return tx.value, sl.value, nb.value
+        bins of 4-angle projector items, slices per projector item) in use"""
+        tx, sl, nb, ps = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().dadmm_launch_shape(self.handle, C.byref(tx), C.byref(sl), C.byref(nb), C.byref(ps)))
+        return tx.value, sl.value, nb.value, ps.value
 
     @property
     def k(self):

@@ -80,7 +80,9 @@ struct Dadmm {
     // tune: 0 wide shapes, 1 timed at the first step and cached per problem shape,
     // 2 narrow shapes
     int tune = 0, bp_tile_x = kBpTileXWide, proj_bins4 = kProjItemBins;
-    int bp_slices = 1;  // batched backprojector items: 1 slice, or 2 slices of one node and tile
+    int bp_slices = 1;    // batched backprojector items: 1 slice, or 2 slices of one node and tile
+    int proj_slices = 1;  // projector items (both forms): 1 slice, or 2 slices of one node
+    int map_rows = kProjRows;  // box height of map_u / map_uT (kProjRows / proj_slices)
     bool tuned = false;
     std::vector<AngRow> angs;           // node-major angle list
     std::vector<int32_t> node_ang_ptr;  // [M + 1]
@@ -667,7 +669,8 @@ static void build_lists(Dadmm& h) {
             const int a0 = h.node_ang_ptr[m], na = h.node_ang_ptr[m + 1] - a0;
             const int sn = sl * M + m;
             h.p_range[2 * sn] = (int)pplain.size();
-            if (na > 0) build_proj_items(*h.g, h.angs, a0, na, sn, sl * A, pplain, h.proj_bins4);
+            if (na > 0 && sl % h.proj_slices == 0)  // slice pairs: the even slice's items cover the next one
+                build_proj_items(*h.g, h.angs, a0, na, sn, sl * A, pplain, h.proj_bins4);
             h.p_range[2 * sn + 1] = (int)pplain.size();
             h.b_range[2 * sn] = (int)bplain.size();
             if (na > 0) build_bp_items(*h.g, a0, na, sn, sl * A, m, sl, bplain, h.bp_tile_x);
@@ -702,7 +705,7 @@ static void build_lists(Dadmm& h) {
     h.d_bplain = device_upload(bplain);
     h.n_pitems = (int)pplain.size();
     h.n_bitems = (int)bbatch.size();
-    h.grid_proj = persistent_grid_project();
+    h.grid_proj = persistent_grid_project(h.proj_slices);
     h.grid_bp = persistent_grid_backproject(true, h.bp_tile_x, h.bp_slices);
     h.drop_graphs();
 }
@@ -787,6 +790,9 @@ static ProjParams proj_params(const Dadmm& h, const dadmm_state& st, const float
     pp.B = h.B;
     pp.ptab = h.g->d_ptab;
     pp.prescale = 1;  // the residual is stored as h_a r_a, the form the backprojector stages
+    pp.map_rows = h.map_rows;
+    pp.pair_img = h.M;   // slice-pair items: the next slice's image of the node
+    pp.pair_rows = h.A;  // ... and its residual lines
     return pp;
 }
 
@@ -849,7 +855,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
             pp.items = h.d_pitems;
             pp.n_items = h.n_pitems;
             pp.counter = w.counters + 2 * e;
-            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s);
+            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s, h.proj_slices);
             mark();
             bp.items = h.d_bitems;
             bp.n_items = h.n_bitems;
@@ -861,7 +867,7 @@ static void enqueue_iteration(Dadmm& h, const dadmm_state& st, const float* sino
                 pp.items = h.d_pplain + h.p_range[2 * sn];
                 pp.n_items = h.p_range[2 * sn + 1] - h.p_range[2 * sn];
                 pp.counter = nullptr;
-                launch_project(pp, pp.n_items, s);
+                launch_project(pp, pp.n_items, s, h.proj_slices);
             }
             mark();
             for (int sn = 0; sn < h.S * h.M; ++sn) {
@@ -1208,10 +1214,13 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                          "unknown tune setting");
             TOMO_REQUIRE(c.tune != DADMM_TUNE_PAIRS || c.S % 2 == 0, "slice pairs need an even number of slices");
             h->tune = c.tune;
-            if (c.tune == DADMM_TUNE_PAIRS) h->bp_slices = 2;
-            if (c.tune == DADMM_TUNE_NARROW || c.tune == DADMM_TUNE_PAIRS) {
+            if (c.tune == DADMM_TUNE_NARROW) {
                 h->bp_tile_x = kBpTileXNarrow;
                 h->proj_bins4 = kProjItemBinsNarrow;
+            }
+            if (c.tune == DADMM_TUNE_PAIRS) {  // narrow backprojector tiles; both operators in slice pairs
+                h->bp_tile_x = kBpTileXNarrow;
+                h->bp_slices = h->proj_slices = 2;
             }
             build_lists(*h);
             // tables
@@ -1308,13 +1317,14 @@ tomo_status dadmm_destroy(dadmm_t hh) {
 
 int dadmm_ring_depth(dadmm_t hh) { return hh ? reinterpret_cast<Dadmm*>(hh)->D : 0; }
 
-tomo_status dadmm_launch_shape(dadmm_t hh, int* bp_tile_x, int* bp_slices, int* proj_item_bins) {
+tomo_status dadmm_launch_shape(dadmm_t hh, int* bp_tile_x, int* bp_slices, int* proj_item_bins, int* proj_slices) {
     return guard([&] {
         Dadmm& h = *as_dadmm(hh);
-        TOMO_REQUIRE(bp_tile_x && bp_slices && proj_item_bins, "output pointers must be non-NULL");
+        TOMO_REQUIRE(bp_tile_x && bp_slices && proj_item_bins && proj_slices, "output pointers must be non-NULL");
         *bp_tile_x = h.bp_tile_x;
         *bp_slices = h.bp_slices;
         *proj_item_bins = h.proj_bins4;
+        *proj_slices = h.proj_slices;
     });
 }
 
@@ -1390,7 +1400,7 @@ namespace tomo {
 static std::mutex g_shape_mu;
 // launch shapes: backprojector tile width and slices per item, projector item bins
 struct Shape {
-    int tile_x, slices, bins4;
+    int tile_x, slices, bins4, pslices;
 };
 static std::map<std::vector<long long>, Shape> g_shape_cache;
 
@@ -1420,30 +1430,33 @@ static std::vector<long long> shape_key(const Dadmm& h) {
 
 // The launch shapes of the problem (the autotuner). tune = 1: once per problem
 // shape and process, at the first step, the candidate shapes are timed on the
-// caller's stream (which this synchronizes): the projector's item widths on the
-// state's u into the residual buffer, then the backprojector's tiles (wide,
-// narrow, and narrow slice pairs when S is even) as the Algorithm 2 step itself
-// with every step size eta1 = 0, so that u is rewritten with its own values
-// (and u^T with their transpose); each twice after a warm-up launch. The
-// fastest shape of each operator is kept and cached. The residual buffer is
-// rewritten by the first inner step before it is read again. tune = 0 / 2 / 3
-// keep the wide / narrow / slice-pair shapes set at create.
+// caller's stream (which this synchronizes): the projector's items (128 or 64
+// bins per angle, and slice pairs when S is even) on the state's u into the
+// residual buffer, then the backprojector's tiles (wide, narrow, and narrow
+// slice pairs when S is even) as the Algorithm 2 step itself with every step
+// size eta1 = 0, so that u is rewritten with its own values (and u^T with
+// their transpose); each twice after a warm-up launch. The fastest shape of
+// each operator is kept and cached. The residual buffer is rewritten by the
+// first inner step before it is read again. tune = 0 / 2 / 3 keep the wide /
+// narrow / slice-pair shapes set at create.
 static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, const WsPtrs& w, cudaStream_t s) {
     h.tuned = true;
     if (h.tune != DADMM_TUNE_AUTO) return;
     const std::vector<long long> key = shape_key(h);
-    Shape pick{0, 0, 0};
+    Shape pick{0, 0, 0, 0};
     {
         std::lock_guard<std::mutex> lk(g_shape_mu);
         auto it = g_shape_cache.find(key);
         if (it != g_shape_cache.end()) pick = it->second;
     }
     if (!pick.tile_x) {
-        // candidates: projector item widths x backprojector tiles (timed separately)
-        const int bins_c[2] = {kProjItemBins, kProjItemBinsNarrow};
-        std::vector<std::pair<int, int>> bp_c = {{kBpTileXWide, 1}, {kBpTileXNarrow, 1}};
-        if (h.S % 2 == 0) bp_c.push_back({kBpTileXNarrow, 2});
-        const int nc = std::max<int>(2, (int)bp_c.size());
+        std::vector<std::pair<int, int>> pj_c = {{kProjItemBins, 1}, {kProjItemBinsNarrow, 1}};  // bins, slices
+        std::vector<std::pair<int, int>> bp_c = {{kBpTileXWide, 1}, {kBpTileXNarrow, 1}};        // tile, slices
+        if (h.S % 2 == 0) {
+            pj_c.push_back({kProjItemBins, 2});
+            bp_c.push_back({kBpTileXNarrow, 2});
+        }
+        const int nc = (int)std::max(pj_c.size(), bp_c.size());
         std::vector<float> tp(nc, INFINITY), tb(nc, INFINITY);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         TOMO_CUDA(cudaEventCreate(&e0));
@@ -1452,11 +1465,19 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
         TOMO_CUDA(ce);
         try {
             for (int c = 0; c < nc; ++c) {
-                h.proj_bins4 = bins_c[std::min(c, 1)];
+                const bool has_pj = c < (int)pj_c.size(), has_bp = c < (int)bp_c.size();
+                h.proj_bins4 = pj_c[std::min<size_t>(c, pj_c.size() - 1)].first;
+                h.proj_slices = pj_c[std::min<size_t>(c, pj_c.size() - 1)].second;
                 h.bp_tile_x = bp_c[std::min<size_t>(c, bp_c.size() - 1)].first;
                 h.bp_slices = bp_c[std::min<size_t>(c, bp_c.size() - 1)].second;
                 build_lists(h);
                 ProjParams pp = proj_params(h, st, sino, w);
+                if (pp.has_map) {  // this candidate's box height
+                    const int rows = kProjRows / h.proj_slices;
+                    pp.has_map = pp.has_mapT = make_image_map(&pp.map, st.u, h.N, h.S * h.M, rows) &&
+                                               make_image_map(&pp.mapT, w.uT, h.N, h.S * h.M, rows);
+                    pp.map_rows = rows;
+                }
                 pp.items = h.d_pitems;
                 pp.n_items = h.n_pitems;
                 pp.counter = w.counters;
@@ -1466,12 +1487,11 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
                 bp.counter = w.counters + 1;
                 bp.view.eta1 = h.d_eta0;
                 for (int op = 0; op < 2; ++op) {
-                    if (op == 0 && c >= 2) continue;  // two projector candidates
-                    if (op == 1 && c >= (int)bp_c.size()) continue;
+                    if ((op == 0 && !has_pj) || (op == 1 && !has_bp)) continue;
                     auto run = [&]() {
                         TOMO_CUDA(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), s));
                         if (op == 0)
-                            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s);
+                            launch_project(pp, std::min(h.grid_proj, h.n_pitems), s, h.proj_slices);
                         else
                             launch_backproject_ustep(bp, std::min(h.grid_bp, h.n_bitems), s, h.bp_tile_x,
                                                      h.bp_slices);
@@ -1494,16 +1514,17 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
         cudaEventDestroy(e1);
         h.ut_dirty = true;  // u^T is rebuilt from u before the first iteration reads it
         const int bi = (int)(std::min_element(tb.begin(), tb.begin() + bp_c.size()) - tb.begin());
-        pick.tile_x = bp_c[bi].first;
-        pick.slices = bp_c[bi].second;
-        pick.bins4 = tp[1] < tp[0] ? bins_c[1] : bins_c[0];
+        const int pi = (int)(std::min_element(tp.begin(), tp.begin() + pj_c.size()) - tp.begin());
+        pick = Shape{bp_c[bi].first, bp_c[bi].second, pj_c[pi].first, pj_c[pi].second};
         std::lock_guard<std::mutex> lk(g_shape_mu);
         g_shape_cache.emplace(key, pick);
     }
-    if (pick.tile_x != h.bp_tile_x || pick.slices != h.bp_slices || pick.bins4 != h.proj_bins4) {
+    if (pick.tile_x != h.bp_tile_x || pick.slices != h.bp_slices || pick.bins4 != h.proj_bins4 ||
+        pick.pslices != h.proj_slices) {
         h.bp_tile_x = pick.tile_x;
         h.bp_slices = pick.slices;
         h.proj_bins4 = pick.bins4;
+        h.proj_slices = pick.pslices;
         build_lists(h);
     }
 }
@@ -1581,8 +1602,12 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
         // TMA descriptors of u and u^T; u^T is rebuilt from u when the state or the
         // workspace changed (or the caller reported writing u), then kept in step by the
         // u-step epilogue
-        const bool maps = make_image_map(&h.map_u, st->u, h.N, h.S * h.M) &&
-                          make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M);
+        auto build_maps = [&]() {
+            h.map_rows = kProjRows / h.proj_slices;
+            return make_image_map(&h.map_u, st->u, h.N, h.S * h.M, h.map_rows) &&
+                   make_image_map(&h.map_uT, w.uT, h.N, h.S * h.M, h.map_rows);
+        };
+        const bool maps = build_maps();
         if (maps != (h.has_maps != 0)) h.drop_graphs();
         h.has_maps = maps ? 1 : 0;
         auto refresh_ut = [&]() {
@@ -1594,7 +1619,10 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
             }
         };
         refresh_ut();  // the autotuner's projector trials read u^T too
-        if (!h.tuned) tune_shapes(h, *st, sino, w, user);
+        if (!h.tuned) {
+            tune_shapes(h, *st, sino, w, user);
+            if (maps) build_maps();  // the chosen shape's box height
+        }
         refresh_ut();
         if (h.mode == DADMM_MODE_BATCHED) {
             const std::vector<const void*> key = {st->u, st->lam, st->xseg, st->hist, st->iter, sino,

@@ -193,16 +193,18 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// one thread: arm the barrier for `bytes` and start the 3-D box load
-__device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar,
-                                             unsigned bytes) {
+// one thread: arm the barrier for count boxes of `bytes` each and start their
+// 3-D loads: box k from image z + k z_step into dst + k dst_step floats
+__device__ __forceinline__ void tma_load_boxes(float* dst, int dst_step, const CUtensorMap* map, int x, int y, int z,
+                                               int z_step, int count, uint64_t* bar, unsigned bytes) {
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
-            (unsigned)__cvta_generic_to_shared(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(b)
-        : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes * count) : "memory");
+    for (int k = 0; k < count; ++k)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+                (unsigned)__cvta_generic_to_shared(dst + k * dst_step)),
+            "l"(map), "r"(x), "r"(y), "r"(z + k * z_step), "r"(b)
+            : "memory");
 }
 
 // nanoseconds of the GPU's global timer
@@ -277,50 +279,65 @@ __device__ __forceinline__ void proj_lane_map(int na, int tid, int& slot, int& b
 
 // NR consecutive rows of one ray inside a staged chunk: the two candidate
 // pixels of each row, weighted by the trapezoid (see the file header); the
-// two candidates accumulate in the two lanes of one packed FP32 pair
-template <int NR>
-__device__ __forceinline__ float ray_rows(const float* base, int f0, const ProjAngle& A) {
-    float2 acc = make_float2(0.f, 0.f);
+// two candidates accumulate in the two lanes of one packed FP32 pair. With
+// PSL slices staged SLF floats apart, the position, weights and address of a
+// row serve every slice; tot[s] gathers slice s
+template <int NR, int PSL, int SLF>
+__device__ __forceinline__ void ray_rows(const float* base, int f0, const ProjAngle& A, float* tot) {
+    float2 acc[PSL];
+#pragma unroll
+    for (int s = 0; s < PSL; ++s) acc[s] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int pl = f0 + r * A.dm25;  // position - J at this row (2^-25), may be negative
         const float F = one_plus_frac25(pl);
         const float* t = base + r * kProjPitch + (pl >> kFracBits);  // lower candidate pixel
-        const float w0 = __saturatef(fmaf(-A.kappa, F, A.wf0));
-        const float w1 = __saturatef(fmaf(A.kappa, F, A.wf1));
-        acc = __ffma2_rn(make_float2(w0, w1), make_float2(t[0], t[1]), acc);
+        const float2 w = make_float2(__saturatef(fmaf(-A.kappa, F, A.wf0)), __saturatef(fmaf(A.kappa, F, A.wf1)));
+#pragma unroll
+        for (int s = 0; s < PSL; ++s) acc[s] = __ffma2_rn(w, make_float2(t[s * SLF], t[s * SLF + 1]), acc[s]);
     }
-    return acc.x + acc.y;
+#pragma unroll
+    for (int s = 0; s < PSL; ++s) tot[s] += acc[s].x + acc[s].y;
 }
 
 // two rays of one angle over the same NR rows, interleaved row by row
-template <int NR>
-__device__ __forceinline__ float2 ray_rows2(const float* base0, int f0, const float* base1, int f1,
-                                            const ProjAngle& A) {
-    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+template <int NR, int PSL, int SLF>
+__device__ __forceinline__ void ray_rows2(const float* base0, int f0, const float* base1, int f1, const ProjAngle& A,
+                                          float* tot0, float* tot1) {
+    float2 acc0[PSL], acc1[PSL];
+#pragma unroll
+    for (int s = 0; s < PSL; ++s) acc0[s] = acc1[s] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int p0 = f0 + r * A.dm25, p1 = f1 + r * A.dm25;
         const float F0 = one_plus_frac25(p0), F1 = one_plus_frac25(p1);
         const float* t0 = base0 + r * kProjPitch + (p0 >> kFracBits);
         const float* t1 = base1 + r * kProjPitch + (p1 >> kFracBits);
-        acc0 = __ffma2_rn(make_float2(__saturatef(fmaf(-A.kappa, F0, A.wf0)), __saturatef(fmaf(A.kappa, F0, A.wf1))),
-                          make_float2(t0[0], t0[1]), acc0);
-        acc1 = __ffma2_rn(make_float2(__saturatef(fmaf(-A.kappa, F1, A.wf0)), __saturatef(fmaf(A.kappa, F1, A.wf1))),
-                          make_float2(t1[0], t1[1]), acc1);
+        const float2 w0 = make_float2(__saturatef(fmaf(-A.kappa, F0, A.wf0)), __saturatef(fmaf(A.kappa, F0, A.wf1)));
+        const float2 w1 = make_float2(__saturatef(fmaf(-A.kappa, F1, A.wf0)), __saturatef(fmaf(A.kappa, F1, A.wf1)));
+#pragma unroll
+        for (int s = 0; s < PSL; ++s) {
+            acc0[s] = __ffma2_rn(w0, make_float2(t0[s * SLF], t0[s * SLF + 1]), acc0[s]);
+            acc1[s] = __ffma2_rn(w1, make_float2(t1[s * SLF], t1[s * SLF + 1]), acc1[s]);
+        }
     }
-    return make_float2(acc0.x + acc0.y, acc1.x + acc1.y);
+#pragma unroll
+    for (int s = 0; s < PSL; ++s) {
+        tot0[s] += acc0[s].x + acc0[s].y;
+        tot1[s] += acc1[s].x + acc1[s].y;
+    }
 }
 
 // staged minor ranges of chunks c0 .. c0 + 31 of the item (warp 0, lane L:
 // chunk c0 + L), written to the ring q0r[chunk & 63]: the first staged column
 // (16-byte aligned) from the lowest corner position over the item's angles;
 // an extent beyond the stage sets *bad (unreachable: the host bounds it)
+template <int R>
 __device__ __forceinline__ void proj_q0_batch(const ProjAngle* sa, int na, int b0, int blast, int m_lo, int c0,
                                               int nch, int lane, int* q0r, int* bad) {
     const int c = c0 + lane;
     if (c >= nch) return;
-    const long long m0 = m_lo + c * kProjRows, m1 = m0 + kProjRows - 1;
+    const long long m0 = m_lo + c * R, m1 = m0 + R - 1;
     long long lo = LLONG_MAX, hi = LLONG_MIN;
     for (int a = 0; a < na; ++a) {
         const ProjAngle& C = sa[a];
@@ -334,13 +351,20 @@ __device__ __forceinline__ void proj_q0_batch(const ProjAngle* sa, int na, int b
     if ((int)(hi >> 40) + 3 - q0 > kProjWMax + 3) atomicOr(bad, 1);
 }
 
+// PSL slices per item (1, or 2: two slices of one node whose rays share the
+// position, weight and address arithmetic; chunks of R = kProjRows / PSL rows,
+// the stages hold both slices' bands, SLF floats apart)
+template <int PSL>
 __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_constant__ ProjParams p) {
+    constexpr int R = kProjRows / PSL;
+    constexpr int SLF = R * kProjPitch;
+    static_assert(PSL * SLF == kProjStageFloats, "a stage holds PSL bands");
     extern __shared__ __align__(1024) unsigned char proj_dyn[];
-    float* stage = reinterpret_cast<float*>(proj_dyn);  // [2][kProjRows][kProjPitch]
+    float* stage = reinterpret_cast<float*>(proj_dyn);  // [2][PSL][R][kProjPitch]
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ ProjAngle sa[kProjMaxNa];
     __shared__ int s_item, s_q0[64], s_bad;  // s_q0: staged range per chunk, a ring of 64
-    __shared__ float s_part[kProjThreads / 2];
+    __shared__ float s_part[PSL][kProjThreads / 2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, B = p.B;
     const size_t n = (size_t)N * N;
@@ -377,40 +401,42 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
         const int b2 = b + 64, bc2 = min(b2, blast);
         const ProjAngle A = sa[slot];
         const int colmaj = sa[0].colmaj;
-        const bool tma = colmaj ? p.has_mapT : p.has_map;
+        const bool tma = (colmaj ? p.has_mapT : p.has_map) && p.map_rows == R;  // else cp.async staging
         const CUtensorMap* map = colmaj ? &p.mapT : &p.map;
         const float* img = p.img + (size_t)item.img * n;
         // this ray's position at the first row of its row group in chunk 0
-        const int r0 = rgrp * (kProjRows / 2);
+        const int r0 = rgrp * (R / 2);
         long long pos = (long long)bc * A.Db + (long long)(item.m_lo + r0) * A.Dm + A.K0;
         long long pos2 = (long long)bc2 * A.Db + (long long)(item.m_lo + r0) * A.Dm + A.K0;
-        const long long dpos = (long long)kProjRows * A.Dm;
-        const int nch = item.nchunks;
-        float total = 0.f, total2 = 0.f;
+        const long long dpos = (long long)R * A.Dm;
+        const int nch = item.nchunks * PSL;  // item.nchunks counts kProjRows-row chunks
+        float total[PSL], total2[PSL];
+#pragma unroll
+        for (int s = 0; s < PSL; ++s) total[s] = total2[s] = 0.f;
 
-        if (warp == 0 && nch > 0) {  // ranges of chunks 0..31; chunk 0's load when TMA is available
-            proj_q0_batch(sa, na, item.b0, blast, item.m_lo, 0, nch, lane, s_q0, &s_bad);
+        if (warp == 0 && nch > 0) {  // ranges of chunks 0..31; chunk 0's loads when TMA is available
+            proj_q0_batch<R>(sa, na, item.b0, blast, item.m_lo, 0, nch, lane, s_q0, &s_bad);
             __syncwarp();
             if (lane == 0 && tma) {
                 fence_proxy_async();
-                tma_load_box(stage, map, s_q0[0], item.m_lo, item.img, &bars[0], 4 * kProjStageFloats);
+                tma_load_boxes(stage, SLF, map, s_q0[0], item.m_lo, item.img, p.pair_img, PSL, &bars[0], 4 * SLF);
             }
         }
         for (int ch = 0; ch < nch; ++ch, pos += dpos, pos2 += dpos) {
             const int sb = ch & 1;
             float* tile = stage + sb * kProjStageFloats;
-            const int m0 = item.m_lo + ch * kProjRows;
+            const int m0 = item.m_lo + ch * R;
             __syncthreads();  // chunk ch-1 consumed by every thread; s_q0[ch & 63] visible
             if (s_bad) break;
-            if (warp == 0 && ch + 1 < nch) {  // next chunk: (TMA) load into the other stage
+            if (warp == 0 && ch + 1 < nch) {  // next chunk: (TMA) loads into the other stage
                 if (((ch + 1) & 31) == 0) {  // ranges of the next 32 chunks (entries 32 back are done)
-                    proj_q0_batch(sa, na, item.b0, blast, item.m_lo, ch + 1, nch, lane, s_q0, &s_bad);
+                    proj_q0_batch<R>(sa, na, item.b0, blast, item.m_lo, ch + 1, nch, lane, s_q0, &s_bad);
                     __syncwarp();
                 }
                 if (lane == 0 && tma) {
                     fence_proxy_async();
-                    tma_load_box(stage + (sb ^ 1) * kProjStageFloats, map, s_q0[(ch + 1) & 63], m0 + kProjRows,
-                                 item.img, &bars[sb ^ 1], 4 * kProjStageFloats);
+                    tma_load_boxes(stage + (sb ^ 1) * kProjStageFloats, SLF, map, s_q0[(ch + 1) & 63], m0 + R,
+                                   item.img, p.pair_img, PSL, &bars[sb ^ 1], 4 * SLF);
                 }
             }
             const int q0 = s_q0[ch & 63];
@@ -425,11 +451,13 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
                 if (!colmaj) {
                     const int ng = kProjPitch / 4;
                     const bool vec = (N & 3) == 0;
-                    for (int r = warp; r < kProjRows; r += kProjThreads / 32) {
+                    for (int e = warp; e < PSL * R; e += kProjThreads / 32) {
+                        const int sl = e / R, r = e - sl * R;
                         const int row = m0 + r;
                         const bool rok = (unsigned)row < (unsigned)N;
-                        const float* src = img + (size_t)(rok ? row : 0) * N;
-                        float* dst = tile + r * kProjPitch;
+                        const float* simg = img + (size_t)sl * p.pair_img * n;
+                        const float* src = simg + (size_t)(rok ? row : 0) * N;
+                        float* dst = tile + sl * SLF + r * kProjPitch;
                         for (int g = lane; g < ng; g += 32) {
                             const int col = q0 + 4 * g;
                             if (vec && rok && col >= 0 && col + 4 <= N) {
@@ -438,18 +466,23 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
                                     const bool ok = rok && (unsigned)(col + e) < (unsigned)N;
-                                    cp_async4(dst + 4 * g + e, ok ? src + col + e : img, ok);
+                                    cp_async4(dst + 4 * g + e, ok ? src + col + e : simg, ok);
                                 }
                             }
                         }
                     }
-                } else {
+                } else if (lane < R) {
                     const int col = m0 + lane;
                     const bool cok = (unsigned)col < (unsigned)N;
-                    for (int q = warp; q < kProjPitch; q += kProjThreads / 32) {
-                        const int row = q0 + q;
-                        const bool ok = cok && (unsigned)row < (unsigned)N;
-                        cp_async4(tile + lane * kProjPitch + q, ok ? img + (size_t)row * N + col : img, ok);
+#pragma unroll
+                    for (int sl = 0; sl < PSL; ++sl) {
+                        const float* simg = img + (size_t)sl * p.pair_img * n;
+                        for (int q = warp; q < kProjPitch; q += kProjThreads / 32) {
+                            const int row = q0 + q;
+                            const bool ok = cok && (unsigned)row < (unsigned)N;
+                            cp_async4(tile + sl * SLF + lane * kProjPitch + q, ok ? simg + (size_t)row * N + col : simg,
+                                      ok);
+                        }
                     }
                 }
                 cp_async_wait_all();
@@ -463,11 +496,11 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
             if (two) {
                 const int J2 = (int)(pos2 >> 40);
                 const int f2 = (int)((pos2 >> (40 - kFracBits)) & ((1 << kFracBits) - 1));
-                const float2 t = ray_rows2<kProjRows>(base, f0, tile + (J2 - q0), f2, A);
-                total += t.x;
-                total2 += t.y;
+                ray_rows2<R, PSL, SLF>(base, f0, tile + (J2 - q0), f2, A, total, total2);
+            } else if (na == 1) {
+                ray_rows<R / 2, PSL, SLF>(base, f0, A, total);
             } else {
-                total += (na == 1) ? ray_rows<kProjRows / 2>(base, f0, A) : ray_rows<kProjRows>(base, f0, A);
+                ray_rows<R, PSL, SLF>(base, f0, A, total);
             }
         }
         if (s_bad) {  // wait (bounded) for a load still in flight before leaving
@@ -479,22 +512,29 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_kernel(const __grid_c
         }
         if (na == 1) {  // add the second row group's partial sums, in a fixed order
             __syncthreads();
-            if (rgrp) s_part[tid & 127] = total;
+#pragma unroll
+            for (int s = 0; s < PSL; ++s)
+                if (rgrp) s_part[s][tid & 127] = total[s];
             __syncthreads();
-            if (!rgrp) total += s_part[tid];
+#pragma unroll
+            for (int s = 0; s < PSL; ++s)
+                if (!rgrp) total[s] += s_part[s][tid];
         }
         if (b < B && !rgrp) {
             const AngRow ar = p.angs[item.ang0 + slot];
-            const size_t o = ((size_t)item.outb + ar.row) * B + b;
-            float v = A.h * total;
-            if (p.sub) v -= __ldg(p.sub + o);
-            if (p.prescale) v *= A.h;
-            p.out[o] = v;
-            if (two && b2 < B) {
-                float v2 = A.h * total2;
-                if (p.sub) v2 -= __ldg(p.sub + o + 64);
-                if (p.prescale) v2 *= A.h;
-                p.out[o + 64] = v2;
+#pragma unroll
+            for (int s = 0; s < PSL; ++s) {
+                const size_t o = ((size_t)item.outb + (size_t)s * p.pair_rows + ar.row) * B + b;
+                float v = A.h * total[s];
+                if (p.sub) v -= __ldg(p.sub + o);
+                if (p.prescale) v *= A.h;
+                p.out[o] = v;
+                if (two && b2 < B) {
+                    float v2 = A.h * total2[s];
+                    if (p.sub) v2 -= __ldg(p.sub + o + 64);
+                    if (p.prescale) v2 *= A.h;
+                    p.out[o + 64] = v2;
+                }
             }
         }
         __syncthreads();  // sa / s_item / s_q0 reused by the next item
@@ -898,13 +938,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg) {
+bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg, int rows) {
     std::memset(map, 0, sizeof(*map));
     const auto fn = tensor_map_encoder();
     if (!fn || ((uintptr_t)base & 15) || (N & 3) || nimg < 1) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)nimg};
     const cuuint64_t strides[2] = {(cuuint64_t)N * 4, (cuuint64_t)N * N * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kProjPitch, (cuuint32_t)kProjRows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)kProjPitch, (cuuint32_t)rows, 1};
     const cuuint32_t elem[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, elem,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -919,15 +959,20 @@ static void ensure_proj_attr() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
+        err = cudaFuncSetAttribute(project_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
     });
     TOMO_CUDA(err);
 }
 
-void launch_project(const ProjParams& p, int grid, cudaStream_t st) {
+void launch_project(const ProjParams& p, int grid, cudaStream_t st, int slices) {
     if (p.n_items == 0) return;
     ensure_proj_attr();
-    project_kernel<<<grid, kProjThreads, proj_smem(), st>>>(p);
+    if (slices == 2)
+        project_kernel<2><<<grid, kProjThreads, proj_smem(), st>>>(p);
+    else
+        project_kernel<1><<<grid, kProjThreads, proj_smem(), st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
@@ -994,11 +1039,12 @@ static int sm_count() {
     return sms;
 }
 
-int persistent_grid_project() {
+int persistent_grid_project(int slices) {
     int per_sm = 0;
     ensure_proj_attr();
-    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel, kProjThreads,
-                                                            proj_smem()));
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, slices == 2 ? (const void*)project_kernel<2> : (const void*)project_kernel<1>, kProjThreads,
+        proj_smem()));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -1354,6 +1400,7 @@ tomo_status tomo_project(tomo_geometry_t gh, const float* img, float* sino, cons
         Geometry::Sel& s = selection(*g, angle_idx, n_sel, batch);
         ProjParams p{};
         p.has_map = make_image_map(&p.map, img, g->N, batch) ? 1 : 0;
+        p.map_rows = kProjRows;
         p.has_mapT = 0;
         p.img = img;
         p.out = sino;

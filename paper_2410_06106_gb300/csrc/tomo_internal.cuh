@@ -207,12 +207,17 @@ struct ProjParams {
     int n_items;
     int N, B;
     int has_map, has_mapT;
+    int map_rows;  // box height of map / mapT; the kernel uses TMA only when it equals its chunk rows
     int prescale;  // 1: write h (h P u - sub), the input the backprojector stages
+    // slice-pair items (two slices of one node share the rays' arithmetic): the
+    // second slice's image index and output line offsets
+    int pair_img, pair_rows;
 };
 
-// TMA descriptor of nimg images [N][N] float32 at base with a 32 x 256 box;
-// false when the layout cannot be described (unaligned base, N % 4 != 0)
-bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg);
+// TMA descriptor of nimg images [N][N] float32 at base with a box of
+// kProjPitch columns x `rows` rows (kProjRows, or kProjRows / 2 for slice
+// pairs); false when the layout cannot be described (unaligned base, N % 4)
+bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg, int rows = kProjRows);
 
 struct BpView {  // dADMM epilogue: where every node's view of x lives
     const float* hist;        // [D][3][S][N][N]
@@ -248,14 +253,15 @@ struct BpParams {
     BpView view;
 };
 
-void launch_project(const ProjParams& p, int grid, cudaStream_t st);
+// slices: 1, or 2 for slice-pair items (chunks of kProjRows / 2 rows)
+void launch_project(const ProjParams& p, int grid, cudaStream_t st, int slices = 1);
 void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st);
 // slices: 1, or 2 for slice-pair items (narrow tiles only)
 void launch_backproject_store(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide,
                               int slices = 1);
 void launch_backproject_ustep(const BpParams& p, int grid, cudaStream_t st, int tile_x = kBpTileXWide,
                               int slices = 1);
-int persistent_grid_project();
+int persistent_grid_project(int slices = 1);
 int persistent_grid_backproject(bool ustep, int tile_x = kBpTileXWide, int slices = 1);
 
 Geometry* as_geometry(tomo_geometry_t g);

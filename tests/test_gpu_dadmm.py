@@ -155,12 +155,13 @@ def test_batched_and_plain_forms_are_bit_identical(quant):
     assert np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("tune,shape", [("wide", (64, 1, 128)), ("narrow", (32, 1, 64)), ("pairs", (32, 2, 64))])
+@pytest.mark.parametrize("tune,shape", [("wide", (64, 1, 128, 1)), ("narrow", (32, 1, 64, 1)),
+                                        ("pairs", (32, 2, 128, 2))])
 def test_launch_shapes_follow_the_oracle(tune, shape):
     """every launch shape of the operators (64 x 64 backprojector tiles with
     128-bin projector items; 32 x 64 tiles with 64-bin items for runs of 4
-    angles; the same with slice-pair backprojector items) by state injection,
-    on two slices; N = 96 leaves ragged tiles in all"""
+    angles; slice pairs of both operators) by state injection, on two slices;
+    N = 96 leaves ragged tiles in all"""
     need_gpu()
     p = small_problem(N=96, A=64, B=139, M=4, S=2, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
     eta = oracle_eta1(p)
@@ -186,27 +187,27 @@ def test_autotuned_shape_is_shared_by_the_solvers_of_a_problem():
     eta = oracle_eta1(p)
     a, b = api.DADMM(p, eta, mode="batched"), api.DADMM(p, eta, mode="plain")
     sino = torch.as_tensor(p["sino"]).cuda()
-    assert a.launch_shape() == (64, 1, 128)  # until the first step
+    assert a.launch_shape() == (64, 1, 128, 1)  # until the first step
     a.step(sino, 3)
     b.step(sino, 3)
-    assert a.launch_shape()[0] == b.launch_shape()[0] and a.launch_shape()[2] == b.launch_shape()[2]
-    assert a.launch_shape() in [(x, 1, n) for x in (32, 64) for n in (64, 128)] + [(32, 2, 64), (32, 2, 128)]
+    sa, sb = a.launch_shape(), b.launch_shape()
+    assert (sa[0], sa[2], sa[3]) == (sb[0], sb[2], sb[3])
+    assert sa[0] in (32, 64) and sa[1] == 1 and sa[2] in (64, 128) and sa[3] == 1  # one slice: no pairs
     for name in ("u", "lam", "xseg", "hist", "iter"):
         assert torch.equal(getattr(a, name), getattr(b, name)), name
 
 
-def test_slice_pairs_equal_single_slice_tiles_bit_for_bit():
-    """slice-pair backprojector items (two slices of a node and tile sharing the
-    position and weight arithmetic) give the same iterates, bit for bit, as
-    single-slice items of the same tiles: batched pairs against the plain form
-    and against batched single-slice narrow tiles, over four slices"""
+def test_slice_pairs_batched_and_plain_are_bit_identical():
+    """with slice-pair items of both operators, the batched form (backprojector
+    pairs) and the plain form (single-slice backprojector tiles of the same
+    shape; the same projector pairs, one launch per slice pair and node) give
+    the same iterates bit for bit, over four slices"""
     need_gpu()
     p = small_problem(N=64, A=48, B=93, M=4, S=4, graph="ring", quant="alternate", noise=0.02, seed=21, km_k=8)
     eta = oracle_eta1(p)
     sino = torch.as_tensor(p["sino"]).cuda()
-    runs = [api.DADMM(p, eta, tune="pairs"), api.DADMM(p, eta, tune="pairs", mode="plain"),
-            api.DADMM(p, eta, tune="narrow")]
-    assert runs[0].launch_shape() == (32, 2, 64) and runs[2].launch_shape() == (32, 1, 64)
+    runs = [api.DADMM(p, eta, tune="pairs"), api.DADMM(p, eta, tune="pairs", mode="plain")]
+    assert runs[0].launch_shape() == (32, 2, 128, 2) == runs[1].launch_shape()
     stats = [r.step(sino, 4) for r in runs]
     for r, st in zip(runs[1:], stats[1:]):
         for name in ("u", "lam", "xseg", "hist", "iter"):
