@@ -274,7 +274,7 @@ typedef struct {
     int max_stale; /* >= 0: extra iterations a held message may age through losses
                       (dadmm_step_lossy); deepens the message ring by as many planes */
     int variant;   /* DADMM_VARIANT_SEGMENTS (Algorithm 4) or DADMM_VARIANT_CONSENSUS */
-    int tune;      /* launch shapes: DADMM_TUNE_WIDE, _AUTO, _NARROW or _PAIRS */
+    int tune;      /* launch shapes: DADMM_TUNE_WIDE, _AUTO, _NARROW, _PAIRS or _QUADS */
 } dadmm_config;
 
 /* Launch shapes of the two operators. Wide: 64 x 64-pixel backprojector tiles
@@ -284,7 +284,8 @@ typedef struct {
  * items (two slices of one node per item, sharing the position and weight
  * arithmetic): the batched backprojector on narrow tiles (the plain form then
  * runs single-slice narrow tiles, with identical results), and the projector
- * in both forms (chunks of 16 rows). Auto: the first dadmm_step of the solver times the shapes of each
+ * in both forms (chunks of 16 rows; groups of 4 slices with chunks of 8 rows
+ * when S is divisible by 4). Auto: the first dadmm_step of the solver times the shapes of each
  * operator on its own state and keeps the fastest (synchronizing the stream once; do not
  * make that first call while the stream is being captured); the choice is
  * cached per device and problem shape for the life of the process, so solvers
@@ -298,6 +299,9 @@ typedef struct {
  * batched form, and slice-pair projector items (128 bins) in both forms
  * (needs an even S) */
 #define DADMM_TUNE_PAIRS 3
+/* wide backprojector tiles, projector items of 4 slices of one node in both
+ * forms (needs S divisible by 4) */
+#define DADMM_TUNE_QUADS 4
 
 /* Algorithm 4: every node owns a segment of x and the segments travel over the
  * graph (the paper's decentralized ADMM). */
@@ -329,8 +333,8 @@ TOMO_API int dadmm_ring_depth(dadmm_t h);
  * slices per batched backprojector item (1, or 2: two slices of one node and
  * tile share the position and weight arithmetic; narrow tiles, even S), bins
  * per angle of 4-angle projector items (128 or 64), and slices per projector
- * item (1, or 2: the rays of two slices of one node share their arithmetic;
- * both forms, even S). With DADMM_TUNE_AUTO these are the wide single-slice
+ * item (1, 2 or 4: the rays of that many slices of one node share their
+ * arithmetic; both forms, S divisible by it). With DADMM_TUNE_AUTO these are the wide single-slice
  * shapes until the first dadmm_step. */
 TOMO_API tomo_status dadmm_launch_shape(dadmm_t h, int* bp_tile_x, int* bp_slices, int* proj_item_bins,
                                         int* proj_slices);

@@ -81,7 +81,7 @@ struct Dadmm {
     // 2 narrow shapes
     int tune = 0, bp_tile_x = kBpTileXWide, proj_bins4 = kProjItemBins;
     int bp_slices = 1;    // batched backprojector items: 1 slice, or 2 slices of one node and tile
-    int proj_slices = 1;  // projector items (both forms): 1 slice, or 2 slices of one node
+    int proj_slices = 1;  // projector items (both forms): 1 slice, or 2 or 4 slices of one node
     int map_rows = kProjRows;  // box height of map_u / map_uT (kProjRows / proj_slices)
     bool tuned = false;
     std::vector<AngRow> angs;           // node-major angle list
@@ -669,7 +669,7 @@ static void build_lists(Dadmm& h) {
             const int a0 = h.node_ang_ptr[m], na = h.node_ang_ptr[m + 1] - a0;
             const int sn = sl * M + m;
             h.p_range[2 * sn] = (int)pplain.size();
-            if (na > 0 && sl % h.proj_slices == 0)  // slice pairs: the even slice's items cover the next one
+            if (na > 0 && sl % h.proj_slices == 0)  // slice groups: the first slice's items cover the group
                 build_proj_items(*h.g, h.angs, a0, na, sn, sl * A, pplain, h.proj_bins4);
             h.p_range[2 * sn + 1] = (int)pplain.size();
             h.b_range[2 * sn] = (int)bplain.size();
@@ -1210,9 +1210,10 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->d_angs = device_upload(angs);
             h->d_bk = device_upload(bp_list_consts(*g, angs));
             TOMO_REQUIRE(c.tune == DADMM_TUNE_WIDE || c.tune == DADMM_TUNE_AUTO || c.tune == DADMM_TUNE_NARROW ||
-                             c.tune == DADMM_TUNE_PAIRS,
+                             c.tune == DADMM_TUNE_PAIRS || c.tune == DADMM_TUNE_QUADS,
                          "unknown tune setting");
             TOMO_REQUIRE(c.tune != DADMM_TUNE_PAIRS || c.S % 2 == 0, "slice pairs need an even number of slices");
+            TOMO_REQUIRE(c.tune != DADMM_TUNE_QUADS || c.S % 4 == 0, "slice quads need S divisible by 4");
             h->tune = c.tune;
             if (c.tune == DADMM_TUNE_NARROW) {
                 h->bp_tile_x = kBpTileXNarrow;
@@ -1222,6 +1223,7 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                 h->bp_tile_x = kBpTileXNarrow;
                 h->bp_slices = h->proj_slices = 2;
             }
+            if (c.tune == DADMM_TUNE_QUADS) h->proj_slices = 4;  // wide backprojector tiles
             build_lists(*h);
             // tables
             std::vector<int32_t> seg_of_row(N);
@@ -1456,6 +1458,7 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
             pj_c.push_back({kProjItemBins, 2});
             bp_c.push_back({kBpTileXNarrow, 2});
         }
+        if (h.S % 4 == 0) pj_c.push_back({kProjItemBins, 4});
         const int nc = (int)std::max(pj_c.size(), bp_c.size());
         std::vector<float> tp(nc, INFINITY), tb(nc, INFINITY);
         cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -351,7 +351,7 @@ __device__ __forceinline__ void proj_q0_batch(const ProjAngle* sa, int na, int b
     if ((int)(hi >> 40) + 3 - q0 > kProjWMax + 3) atomicOr(bad, 1);
 }
 
-// PSL slices per item (1, or 2: two slices of one node whose rays share the
+// PSL slices per item (1, 2 or 4 slices of one node whose rays share the
 // position, weight and address arithmetic; chunks of R = kProjRows / PSL rows,
 // the stages hold both slices' bands, SLF floats apart)
 template <int PSL>
@@ -962,6 +962,8 @@ static void ensure_proj_attr() {
         err = cudaFuncSetAttribute(project_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(project_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem());
     });
     TOMO_CUDA(err);
 }
@@ -969,7 +971,9 @@ static void ensure_proj_attr() {
 void launch_project(const ProjParams& p, int grid, cudaStream_t st, int slices) {
     if (p.n_items == 0) return;
     ensure_proj_attr();
-    if (slices == 2)
+    if (slices == 4)
+        project_kernel<4><<<grid, kProjThreads, proj_smem(), st>>>(p);
+    else if (slices == 2)
         project_kernel<2><<<grid, kProjThreads, proj_smem(), st>>>(p);
     else
         project_kernel<1><<<grid, kProjThreads, proj_smem(), st>>>(p);
@@ -1042,9 +1046,10 @@ static int sm_count() {
 int persistent_grid_project(int slices) {
     int per_sm = 0;
     ensure_proj_attr();
-    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, slices == 2 ? (const void*)project_kernel<2> : (const void*)project_kernel<1>, kProjThreads,
-        proj_smem()));
+    const void* fn = slices == 4   ? (const void*)project_kernel<4>
+                     : slices == 2 ? (const void*)project_kernel<2>
+                                   : (const void*)project_kernel<1>;
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kProjThreads, proj_smem()));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 

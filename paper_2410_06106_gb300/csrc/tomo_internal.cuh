@@ -209,14 +209,14 @@ struct ProjParams {
     int has_map, has_mapT;
     int map_rows;  // box height of map / mapT; the kernel uses TMA only when it equals its chunk rows
     int prescale;  // 1: write h (h P u - sub), the input the backprojector stages
-    // slice-pair items (two slices of one node share the rays' arithmetic): the
-    // second slice's image index and output line offsets
+    // slice-group items (slices of one node share the rays' arithmetic): the
+    // image index and output line offsets from one slice to the next
     int pair_img, pair_rows;
 };
 
 // TMA descriptor of nimg images [N][N] float32 at base with a box of
-// kProjPitch columns x `rows` rows (kProjRows, or kProjRows / 2 for slice
-// pairs); false when the layout cannot be described (unaligned base, N % 4)
+// kProjPitch columns x `rows` rows (kProjRows, or kProjRows / slices for
+// slice groups); false when the layout cannot be described (unaligned base, N % 4)
 bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg, int rows = kProjRows);
 
 struct BpView {  // dADMM epilogue: where every node's view of x lives
@@ -253,7 +253,7 @@ struct BpParams {
     BpView view;
 };
 
-// slices: 1, or 2 for slice-pair items (chunks of kProjRows / 2 rows)
+// slices: 1, or 2 / 4 for slice-group items (chunks of kProjRows / slices rows)
 void launch_project(const ProjParams& p, int grid, cudaStream_t st, int slices = 1);
 void launch_transpose(const float* in, float* out, int N, int nimg, cudaStream_t st);
 // slices: 1, or 2 for slice-pair items (narrow tiles only)

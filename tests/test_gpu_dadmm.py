@@ -156,14 +156,14 @@ def test_batched_and_plain_forms_are_bit_identical(quant):
 
 
 @pytest.mark.parametrize("tune,shape", [("wide", (64, 1, 128, 1)), ("narrow", (32, 1, 64, 1)),
-                                        ("pairs", (32, 2, 128, 2))])
+                                        ("pairs", (32, 2, 128, 2)), ("quads", (64, 1, 128, 4))])
 def test_launch_shapes_follow_the_oracle(tune, shape):
     """every launch shape of the operators (64 x 64 backprojector tiles with
     128-bin projector items; 32 x 64 tiles with 64-bin items for runs of 4
-    angles; slice pairs of both operators) by state injection, on two slices;
-    N = 96 leaves ragged tiles in all"""
+    angles; slice pairs of both operators; projector items of 4 slices) by
+    state injection, on four slices; N = 96 leaves ragged tiles in all"""
     need_gpu()
-    p = small_problem(N=96, A=64, B=139, M=4, S=2, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
+    p = small_problem(N=96, A=64, B=139, M=4, S=4, graph="ring", quant="alternate", noise=0.02, seed=12, km_k=16)
     eta = oracle_eta1(p)
     s = api.DADMM(p, eta, tune=tune)
     assert s.launch_shape() == shape
@@ -208,6 +208,12 @@ def test_slice_pairs_batched_and_plain_are_bit_identical():
     sino = torch.as_tensor(p["sino"]).cuda()
     runs = [api.DADMM(p, eta, tune="pairs"), api.DADMM(p, eta, tune="pairs", mode="plain")]
     assert runs[0].launch_shape() == (32, 2, 128, 2) == runs[1].launch_shape()
+    quads = [api.DADMM(p, eta, tune="quads"), api.DADMM(p, eta, tune="quads", mode="plain")]
+    assert quads[0].launch_shape() == (64, 1, 128, 4)
+    qst = [r.step(sino, 4) for r in quads]
+    for name in ("u", "lam", "xseg", "hist", "iter"):
+        assert torch.equal(getattr(quads[0], name), getattr(quads[1], name)), name
+    assert np.array_equal(qst[0], qst[1])
     stats = [r.step(sino, 4) for r in runs]
     for r, st in zip(runs[1:], stats[1:]):
         for name in ("u", "lam", "xseg", "hist", "iter"):
