@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--cpu-nodes", type=int, default=64, help="oracle sample: nodes of slice 0")
     ap.add_argument("--ref-nodes", type=int, default=8, help="reference arm: nodes of slice 0 per step")
     ap.add_argument("--slices", type=int, default=None, help="override the number of slices")
-    ap.add_argument("--tune", choices=["auto", "wide", "narrow", "pairs", "quads"], default="auto",
+    ap.add_argument("--tune", choices=["auto", "wide", "narrow", "pairs", "quads", "widepairs"], default="auto",
                     help="launch shapes of the operators (auto: timed at the first step)")
     ap.add_argument("--quick-eta", action="store_true",
                     help="step sizes from the bound ||P_m||^2 <= 1.2 A_m N instead of power iterations")

@@ -274,7 +274,7 @@ typedef struct {
     int max_stale; /* >= 0: extra iterations a held message may age through losses
                       (dadmm_step_lossy); deepens the message ring by as many planes */
     int variant;   /* DADMM_VARIANT_SEGMENTS (Algorithm 4) or DADMM_VARIANT_CONSENSUS */
-    int tune;      /* launch shapes: DADMM_TUNE_WIDE, _AUTO, _NARROW, _PAIRS or _QUADS */
+    int tune;      /* launch shapes: DADMM_TUNE_WIDE, _AUTO, _NARROW, _PAIRS, _QUADS or _WIDE_PAIRS */
 } dadmm_config;
 
 /* Launch shapes of the two operators. Wide: 64 x 64-pixel backprojector tiles
@@ -302,6 +302,9 @@ typedef struct {
 /* wide backprojector tiles, projector items of 4 slices of one node in both
  * forms (needs S divisible by 4) */
 #define DADMM_TUNE_QUADS 4
+/* wide backprojector tiles in slice pairs (batched form), projector items of 4
+ * slices (needs S divisible by 4) */
+#define DADMM_TUNE_WIDE_PAIRS 5
 
 /* Algorithm 4: every node owns a segment of x and the segments travel over the
  * graph (the paper's decentralized ADMM). */
@@ -331,7 +334,7 @@ TOMO_API int dadmm_ring_depth(dadmm_t h);
 
 /* The launch shapes in use: backprojector tile width in pixels (64 or 32),
  * slices per batched backprojector item (1, or 2: two slices of one node and
- * tile share the position and weight arithmetic; narrow tiles, even S), bins
+ * tile share the position and weight arithmetic; even S), bins
  * per angle of 4-angle projector items (128 or 64), and slices per projector
  * item (1, 2 or 4: the rays of that many slices of one node share their
  * arithmetic; both forms, S divisible by it). With DADMM_TUNE_AUTO these are the wide single-slice

@@ -310,8 +310,9 @@ class DADMM:
     def __init__(self, prob, eta1, mode="batched", geometry=None, tune="auto"):
         """tune: launch shapes, "auto" (timed at the first step, cached per
         problem shape in the process), "wide", "narrow", "pairs" (slice pairs of
-        both operators, even S) or "quads" (projector items of 4 slices, S % 4
-        == 0); see dadmm_config"""
+        both operators, even S), "quads" (projector items of 4 slices, S % 4
+        == 0) or "widepairs" (quads with wide backprojector tiles in slice
+        pairs); see dadmm_config"""
         g = prob["geometry"]
         self.N, self.B, self.A = g["N"], g["B"], g["A"]
         self.S, self.M = int(prob["S"]), int(prob["M"])
@@ -343,9 +344,9 @@ class DADMM:
         if self.variant not in ("segments", "consensus"):
             raise TomoError(-1, "variant must be 'segments' or 'consensus'")
         cfg.variant = 1 if self.variant == "consensus" else 0
-        tunes = {"wide": 0, "auto": 1, "narrow": 2, "pairs": 3, "quads": 4}
+        tunes = {"wide": 0, "auto": 1, "narrow": 2, "pairs": 3, "quads": 4, "widepairs": 5}
         if tune not in tunes:
-            raise TomoError(-1, "tune must be 'auto', 'wide', 'narrow', 'pairs' or 'quads'")
+            raise TomoError(-1, "tune must be 'auto', 'wide', 'narrow', 'pairs', 'quads' or 'widepairs'")
         cfg.tune = tunes[tune]
         self.mode = mode
         self.cfg = cfg

@@ -1210,10 +1210,12 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             h->d_angs = device_upload(angs);
             h->d_bk = device_upload(bp_list_consts(*g, angs));
             TOMO_REQUIRE(c.tune == DADMM_TUNE_WIDE || c.tune == DADMM_TUNE_AUTO || c.tune == DADMM_TUNE_NARROW ||
-                             c.tune == DADMM_TUNE_PAIRS || c.tune == DADMM_TUNE_QUADS,
+                             c.tune == DADMM_TUNE_PAIRS || c.tune == DADMM_TUNE_QUADS ||
+                             c.tune == DADMM_TUNE_WIDE_PAIRS,
                          "unknown tune setting");
             TOMO_REQUIRE(c.tune != DADMM_TUNE_PAIRS || c.S % 2 == 0, "slice pairs need an even number of slices");
-            TOMO_REQUIRE(c.tune != DADMM_TUNE_QUADS || c.S % 4 == 0, "slice quads need S divisible by 4");
+            TOMO_REQUIRE((c.tune != DADMM_TUNE_QUADS && c.tune != DADMM_TUNE_WIDE_PAIRS) || c.S % 4 == 0,
+                         "slice quads need S divisible by 4");
             h->tune = c.tune;
             if (c.tune == DADMM_TUNE_NARROW) {
                 h->bp_tile_x = kBpTileXNarrow;
@@ -1224,6 +1226,10 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
                 h->bp_slices = h->proj_slices = 2;
             }
             if (c.tune == DADMM_TUNE_QUADS) h->proj_slices = 4;  // wide backprojector tiles
+            if (c.tune == DADMM_TUNE_WIDE_PAIRS) {  // wide backprojector tiles in slice pairs
+                h->bp_slices = 2;
+                h->proj_slices = 4;
+            }
             build_lists(*h);
             // tables
             std::vector<int32_t> seg_of_row(N);
@@ -1457,6 +1463,7 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
         if (h.S % 2 == 0) {
             pj_c.push_back({kProjItemBins, 2});
             bp_c.push_back({kBpTileXNarrow, 2});
+            bp_c.push_back({kBpTileXWide, 2});
         }
         if (h.S % 4 == 0) pj_c.push_back({kProjItemBins, 4});
         const int nc = (int)std::max(pj_c.size(), bp_c.size());

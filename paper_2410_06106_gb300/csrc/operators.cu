@@ -613,13 +613,12 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
 __host__ __device__ constexpr int bp_threads(int slices) { return slices == 2 ? 256 : kBpThreads; }
 
 template <int EPI, int PX, int SL>
-__global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? 3 : 4) backproject_kernel(const BpParams p) {
+__global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 4) backproject_kernel(const BpParams p) {
     constexpr int NT = bp_threads(SL);
     constexpr int TY = NT / 16;          // thread rows
     constexpr int RPT = kBpTileY / TY;   // pixel rows per thread (8, or 4 for slice pairs)
     constexpr int TX = 16 * PX;          // tile width
     constexpr int CH = kBpChunk / SL;    // angles per chunk: a stage holds SL windows per angle
-    static_assert(SL == 1 || PX == 2, "slice pairs use the narrow tiles (registers)");
     extern __shared__ __align__(16) unsigned char bp_dyn[];
     float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][SL][CH][kBpWin]
     __shared__ BpConst s_k[CH];                        // constants of the chunk after next
@@ -1001,6 +1000,8 @@ static void ensure_bp_attr() {
         if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2, 1>();
         if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 2, 2>();
         if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 2, 2>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_STORE, 4, 2>();
+        if (err == cudaSuccess) err = set_bp_attr<EPI_USTEP, 4, 2>();
     });
     TOMO_CUDA(err);
 }
@@ -1008,7 +1009,9 @@ static void ensure_bp_attr() {
 // the instantiation of a launch shape
 template <int EPI>
 static const void* bp_kernel_fn(int tile_x, int slices) {
-    if (slices == 2) return (const void*)backproject_kernel<EPI, 2, 2>;
+    if (slices == 2)
+        return tile_x == kBpTileXNarrow ? (const void*)backproject_kernel<EPI, 2, 2>
+                                        : (const void*)backproject_kernel<EPI, 4, 2>;
     return tile_x == kBpTileXNarrow ? (const void*)backproject_kernel<EPI, 2, 1>
                                     : (const void*)backproject_kernel<EPI, 4, 1>;
 }
@@ -1018,8 +1021,10 @@ static void launch_bp(const BpParams& p, int grid, cudaStream_t st, int tile_x, 
     if (p.n_items == 0) return;
     ensure_bp_attr();
     if (slices == 2) {
-        if (tile_x != kBpTileXNarrow) fail(TOMO_ERR_INVALID_ARG, "slice pairs need the narrow tiles");
-        backproject_kernel<EPI, 2, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
+        if (tile_x == kBpTileXNarrow)
+            backproject_kernel<EPI, 2, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
+        else
+            backproject_kernel<EPI, 4, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
     } else if (tile_x == kBpTileXNarrow) {
         backproject_kernel<EPI, 2, 1><<<grid, kBpThreads, kBpSmem, st>>>(p);
     } else {

@@ -156,7 +156,8 @@ def test_batched_and_plain_forms_are_bit_identical(quant):
 
 
 @pytest.mark.parametrize("tune,shape", [("wide", (64, 1, 128, 1)), ("narrow", (32, 1, 64, 1)),
-                                        ("pairs", (32, 2, 128, 2)), ("quads", (64, 1, 128, 4))])
+                                        ("pairs", (32, 2, 128, 2)), ("quads", (64, 1, 128, 4)),
+                                        ("widepairs", (64, 2, 128, 4))])
 def test_launch_shapes_follow_the_oracle(tune, shape):
     """every launch shape of the operators (64 x 64 backprojector tiles with
     128-bin projector items; 32 x 64 tiles with 64-bin items for runs of 4
@@ -208,8 +209,8 @@ def test_slice_pairs_batched_and_plain_are_bit_identical():
     sino = torch.as_tensor(p["sino"]).cuda()
     runs = [api.DADMM(p, eta, tune="pairs"), api.DADMM(p, eta, tune="pairs", mode="plain")]
     assert runs[0].launch_shape() == (32, 2, 128, 2) == runs[1].launch_shape()
-    quads = [api.DADMM(p, eta, tune="quads"), api.DADMM(p, eta, tune="quads", mode="plain")]
-    assert quads[0].launch_shape() == (64, 1, 128, 4)
+    quads = [api.DADMM(p, eta, tune="widepairs"), api.DADMM(p, eta, tune="widepairs", mode="plain")]
+    assert quads[0].launch_shape() == (64, 2, 128, 4)  # the plain form runs single-slice wide tiles
     qst = [r.step(sino, 4) for r in quads]
     for name in ("u", "lam", "xseg", "hist", "iter"):
         assert torch.equal(getattr(quads[0], name), getattr(quads[1], name)), name
