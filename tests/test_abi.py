@@ -47,3 +47,17 @@ def test_calls_without_gpu_fail_loudly(libpath):
     from paper_2410_06106_gb300 import api
     with pytest.raises(api.TomoError):
         api.Geometry(8, 13, A=4)
+
+
+def test_binding_constants_match_header():
+    """the binding's mode, variant and launch-shape codes are the header's"""
+    from paper_2410_06106_gb300 import api
+    src = open(HEADER).read()
+    defs = dict((k, int(v)) for k, v in re.findall(r"#define\s+(DADMM_\w+)\s+(-?\d+)", src))
+    assert defs["DADMM_MODE_BATCHED"] == api.MODE_BATCHED and defs["DADMM_MODE_PLAIN"] == api.MODE_PLAIN
+    assert defs["DADMM_VARIANT_SEGMENTS"] == 0 and defs["DADMM_VARIANT_CONSENSUS"] == 1
+    tunes = {"wide": "DADMM_TUNE_WIDE", "auto": "DADMM_TUNE_AUTO", "narrow": "DADMM_TUNE_NARROW",
+             "pairs": "DADMM_TUNE_PAIRS", "quads": "DADMM_TUNE_QUADS", "widepairs": "DADMM_TUNE_WIDE_PAIRS"}
+    code = open(os.path.join(ROOT, "paper_2410_06106_gb300", "api.py")).read()
+    mapping = dict(re.findall(r'"(\w+)": (\d+)', code[code.index("tunes = {"):code.index("}", code.index("tunes = {"))]))
+    assert {k: int(v) for k, v in mapping.items()} == {k: defs[v] for k, v in tunes.items()}
