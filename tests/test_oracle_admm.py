@@ -3,8 +3,10 @@ against consequences of the mathematics: a single node reduces to
 least squares (dense lstsq), exact noise-free data is a fixed point even with
 relay delays, exactly solved sub-problems satisfy the optimality
 conditions of Eq. 15-16 and zero the owner's dual (Eq. 18), the x-update has a closed form, the relay tables
-of a 4-ring are known by hand, and the view every node uses carries exactly
-the hop delay and quantizer the graph dictates."""
+of a 4-ring are known by hand, the view every node uses carries exactly
+the hop delay and quantizer the graph dictates, and the FP64 statistics
+(primal gap, change and norm of node 0's view, residual) equal their values
+worked out by hand from the state."""
 import numpy as np
 import pytest
 
@@ -167,3 +169,120 @@ def test_jpeg_bytes_are_the_entropy_coded_messages():
         eb = len(O.jpeg_entropy(coefs)) if lohi[1] > lohi[0] else 0
         want += (M - 1) * (eb + 8)
     assert stats[0, 4] == want
+
+
+# ---------------------------------------------------------------------------
+# the FP64 statistics of an iteration: [gap2, chg2, nrm2, resid2, bytes]
+# (Sec. 3.2's stopping quantity and the residual, read as in the oracle's
+# header), pinned against values that follow from the state by hand
+# ---------------------------------------------------------------------------
+
+def ring4_dist(s, m):
+    d = abs(s - m)
+    return min(d, 4 - d)
+
+
+def test_residual_statistic_from_zero_is_the_data_norm():
+    """From u = 0 with E1 = 1 the only inner step's residual is -d_m, so the
+    statistic is sum_m ||d_m||^2 = ||d||^2 (the subsets partition the angles)"""
+    p = small_problem(N=8, A=16, B=13, M=3, graph="complete", E1=1, noise=0.05, seed=5)
+    st = O.DADMM(p, oracle_eta1(p))
+    stats = st.iterate(p["sino"])
+    d = p["sino"][0].astype(np.float64)
+    assert abs(stats[0, 3] - np.sum(d * d)) <= 1e-13 * np.sum(d * d)
+
+
+def test_residual_statistic_is_taken_at_the_last_inner_step():
+    """E1 = 2 from zero: the first step gives u_m = eta1_m P_m^T d_m (x = lambda = 0),
+    and the statistic is the second step's residual
+    sum_m ||eta1_m P_m P_m^T d_m - d_m||^2, evaluated here with dense matrices"""
+    N, B, A, M = 8, 13, 16, 2
+    p = small_problem(N=N, A=A, B=B, M=M, graph="complete", E1=2, noise=0.05, seed=8)
+    eta = oracle_eta1(p)
+    st = O.DADMM(p, eta)
+    stats = st.iterate(p["sino"])
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    want = 0.0
+    for m in range(M):
+        sel = idx[ptr[m]:ptr[m + 1]]
+        P = dense_P(geo, N, sel)
+        dm = p["sino"][0][sel].astype(np.float64).ravel()
+        r = eta[m] * (P @ (P.T @ dm)) - dm
+        want += float(r @ r)
+    assert abs(stats[0, 3] - want) <= 1e-12 * want
+
+
+@pytest.mark.parametrize("quant", ["none", "alternate"])
+def test_change_norm_and_gap_statistics_follow_the_views(quant):
+    """Ring of 4, E1 = 0, u = lambda = 0: the x-update gives x[m] = f X on
+    every segment (f = (1 - eta2 rho)^E2, Algorithm 3 with v = 0), so every
+    view is known by hand from the relay delays of the 4-ring (segment s
+    reaches node m max(dist - 1, 0) iterations late). Then
+      chg2 = ||x_0^{k+1} - x_0^k||^2 and nrm2 = ||x_0^k||^2 (node 0's views),
+      gap2 = sum_m ||u_m - x_m^{k+1}||^2 = sum_m ||x_m^{k+1}||^2,
+      resid2 = 0 (no inner step).
+    Every stored version of every segment is a distinct constant, so a view
+    read at the wrong iteration or from the wrong plane changes chg2 or nrm2.
+    Constant segments pass every quantizer exactly (as their FP32 value)."""
+    N, M, rho, eta2, E2, k = 8, 4, 0.7, 0.3, 3, 5
+    p = small_problem(N=N, M=M, graph="ring", quant=quant, E1=0, E2=E2, rho=rho, eta2=eta2)
+    st = O.DADMM(p, np.ones(M))
+    D = st.D
+    seg = p["seg_row_ptr"]
+    hist = np.zeros((D, 3, 1, N, N))
+    X = np.zeros((1, N, N))
+    for s in range(M):
+        X[0, seg[s]:seg[s + 1]] = 3.0 + s
+        for j in range(D):
+            for q in range(3):
+                hist[j, q, 0, seg[s]:seg[s + 1]] = 1.0 + 0.5 * q + 0.25 * j + 0.01 * s
+    st.load_state(np.zeros((1, M, N, N)), np.zeros((1, M, N, N)), X, hist, k)
+    stats = st.iterate(np.zeros((1, 16, 13), np.float32))
+    f = (1.0 - eta2 * rho) ** E2
+    adj = p["adj"]
+
+    def kind(s, m):
+        if s == m:
+            return p["home_q"][m]
+        # first edge of the lowest-id-parent shortest path on the 4-ring: the
+        # neighbour of s towards m (for the opposite node, the lower-id neighbour)
+        nbrs = [t for t in range(M) if adj[s, t]]
+        first = min(t for t in nbrs if ring4_dist(t, m) == ring4_dist(s, m) - 1)
+        return p["edge_q"][s, first]
+
+    def view(m, it):
+        out = np.zeros((N, N))
+        for s in range(M):
+            lag = 0 if s == m else ring4_dist(s, m) - 1
+            ver = it - lag
+            if ver == k + 1:  # the fresh message; the quantizers code the FP32 segment
+                v = f * (3.0 + s)
+                out[seg[s]:seg[s + 1]] = v if kind(s, m) == 0 else float(np.float32(v))
+            else:
+                out[seg[s]:seg[s + 1]] = hist[ver % D, kind(s, m), 0, seg[s]:seg[s + 1]]
+        return out
+
+    v1, v0 = view(0, k + 1), view(0, k)
+    assert np.isclose(stats[0, 1], np.sum((v1 - v0) ** 2), rtol=1e-13, atol=0)
+    assert np.isclose(stats[0, 2], np.sum(v0 ** 2), rtol=1e-13, atol=0)
+    gap = sum(np.sum(view(m, k + 1) ** 2) for m in range(M))
+    assert np.isclose(stats[0, 0], gap, rtol=1e-13, atol=0)
+    assert stats[0, 3] == 0.0
+
+
+def test_change_statistic_over_the_first_two_iterations():
+    """Complete graph, no quantizer: node 0's view is the owners'
+    reconstruction. After iteration 1 from zero nrm2 = 0 and
+    chg2 = ||x^1||^2; after iteration 2 nrm2 = ||x^1||^2 and
+    chg2 = ||x^2 - x^1||^2"""
+    p = small_problem(N=16, A=24, B=23, M=4, graph="complete", noise=0.02, seed=11)
+    st = O.DADMM(p, oracle_eta1(p))
+    s1 = st.iterate(p["sino"])
+    x1 = st.home_view()
+    s2 = st.iterate(p["sino"])
+    x2 = st.home_view()
+    assert s1[0, 2] == 0.0
+    assert np.isclose(s1[0, 1], np.sum(x1 * x1), rtol=1e-13, atol=0)
+    assert np.isclose(s2[0, 2], np.sum(x1 * x1), rtol=1e-13, atol=0)
+    assert np.isclose(s2[0, 1], np.sum((x2 - x1) ** 2), rtol=1e-12, atol=0)
