@@ -25,23 +25,17 @@ static __device__ __align__(256) unsigned char g_noalloc_worklist[kNoAllocBytes]
 
 // Device address of the array on the current device. In host code the symbol
 // g_noalloc_worklist is only a host-side stand-in, so its address must be
-// asked from the runtime (once per device, with that device current); a
-// kernel handed the host symbol would fault or read the wrong memory.
+// asked from the runtime, with the device current; a kernel handed the host
+// symbol would fault or read the wrong memory. The address is looked up on
+// every call (the lookup allocates nothing) rather than cached, so it stays
+// right if the caller tears down and re-creates a device's context. The
+// first lookup on a device may load the library's module there.
 static unsigned char* noalloc_worklist_address() {
-    static std::mutex mu;
-    static unsigned char* addr[64] = {nullptr};
-    int dev = 0;
-    TOMO_CUDA(cudaGetDevice(&dev));
-    TOMO_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_worklist);
-        if (e != cudaSuccess || p == nullptr)
-            fail(TOMO_ERR_CUDA, std::string("cudaGetSymbolAddress(work-list array): ") + cudaGetErrorString(e));
-        addr[dev] = static_cast<unsigned char*>(p);
-    }
-    return addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_worklist);
+    if (e != cudaSuccess || p == nullptr)
+        fail(TOMO_ERR_CUDA, std::string("cudaGetSymbolAddress(work-list array): ") + cudaGetErrorString(e));
+    return static_cast<unsigned char*>(p);
 }
 
 }  // namespace tomo
@@ -59,6 +53,14 @@ tomo_status tomo_project_noalloc(tomo_geometry_t gh, const float* img, float* si
         TOMO_REQUIRE(batch >= 1, "batch must be >= 1");
         TOMO_REQUIRE(n_sel >= 1, "n_sel must be >= 1");
         TOMO_REQUIRE(angle_idx || n_sel == g->A, "angle_idx NULL requires n_sel == n_angles");
+        cudaStream_t st = (cudaStream_t)stream;
+        // the work list is copied from host buffers that live only for this call, so the
+        // copies must run now, not be recorded into a graph that replays them later
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        TOMO_CUDA(cudaStreamIsCapturing(st, &cap));
+        TOMO_REQUIRE(cap == cudaStreamCaptureStatusNone,
+                     "tomo_project_noalloc: the stream is capturing a CUDA graph; the call copies its work "
+                     "list from host memory it does not keep, so it refuses to be captured");
         if (n_sel > kNoAllocMaxAngles)
             fail(TOMO_ERR_WORKSPACE, "tomo_project_noalloc: " + std::to_string(n_sel) +
                                          " angles exceed the fixed work-list capacity of " +
@@ -78,7 +80,6 @@ tomo_status tomo_project_noalloc(tomo_geometry_t gh, const float* img, float* si
         unsigned char* base = noalloc_worklist_address();
         ProjItem* d_items = reinterpret_cast<ProjItem*>(base);
         AngRow* d_angs = reinterpret_cast<AngRow*>(base + kNoAllocItemBytes);
-        cudaStream_t st = (cudaStream_t)stream;
         // pageable sources: each copy has read its host buffer when it returns
         TOMO_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(ProjItem) * items.size(), cudaMemcpyHostToDevice, st));
         TOMO_CUDA(cudaMemcpyAsync(d_angs, angs.data(), sizeof(AngRow) * angs.size(), cudaMemcpyHostToDevice, st));
