@@ -37,6 +37,8 @@ METRIC = "projector+backprojector GUPS and ADMM iter/s, batched vs plain on 1 GB
 UNIT = "GUPS"
 FLOP_PER_UPDATE = 8.0  # 2 touched bins x (ramp FMA + weight x value FMA)
 FP32_LANES_PER_SM = 128
+# backprojector + u-step: u, lambda, the node's view of x read; u and u^T written
+BP_BYTES_PER_PIXEL_NODE = 20.0
 
 
 def parse():
@@ -269,6 +271,7 @@ def run_ours(args, ws, rank, local):
     else:
         L = np.array([geo.opnorm_sq(idx[ptr[m]:ptr[m + 1]], iters=20) for m in range(prob["M"])])
     eta1 = 1.0 / (L + prob["rho"])
+    fma_peak = api.fp32_peak(50)  # the FP32 roofline denominator, measured on this GPU before the run
     sino_host = torch.as_tensor(prob["sino"]).pin_memory()
     sino = sino_host.to(dev)
     upd = updates_per_iteration(prob)
@@ -316,9 +319,24 @@ def run_ours(args, ws, rank, local):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tflops = sms * FP32_LANES_PER_SM * 2.0 * sm_max * 1e6 / 1e12
+    nominal_tflops = sms * FP32_LANES_PER_SM * 2.0 * sm_max * 1e6 / 1e12
+    peak_tflops = max(fma_peak["scalar_tflops"], fma_peak["packed_tflops"])
     achieved = FLOP_PER_UPDATE * upd_per_launch / (dom_ms * 1e-3) / 1e12
     traffic = profile_traffic(dominant)
+    # algorithmic HBM bytes per launch (4-byte values; each array once): the projector
+    # reads every node's image once (u, or its transpose for steep rays) plus d and
+    # writes the residual; the backprojector + u-step reads u, lambda and the node's
+    # view of x and writes u and u^T, and reads the residual
+    S, M, N, A, B = prob["S"], prob["M"], g["N"], g["A"], g["B"]
+    pix = float(S) * M * N * N
+    bytes_launch = {"project": 4.0 * pix + 8.0 * S * A * B,
+                    "backproject_ustep": BP_BYTES_PER_PIXEL_NODE * pix + 4.0 * S * A * B}
+    hbm_peak = float(peaks.get("hbm_gbs", 0.0)) or None
+    hbm = {}
+    for kname, kms in (("project", pj_ms), ("backproject_ustep", bp_ms)):
+        gbs = bytes_launch[kname] / (kms * 1e-3) / 1e9
+        hbm[kname] = {"bytes_per_launch": bytes_launch[kname], "achieved_gbs": gbs,
+                      "frac": gbs / hbm_peak if hbm_peak else None}
 
     plain = None
     if not args.no_plain:
@@ -411,8 +429,14 @@ def run_ours(args, ws, rank, local):
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                              "ms_per_launch": dom_ms, "updates_per_launch": upd_per_launch,
                              "flop_per_update": FLOP_PER_UPDATE,
-                             "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock of "
-                                           "MEASURED_PEAKS.json)" % (sms, FP32_LANES_PER_SM, sm_max),
+                             "peak_basis": "measured: FP32 FMA microbenchmark (tomo_fp32_peak), best of "
+                                           "scalar %.1f and packed %.1f TFLOP/s at %.0f MHz; nominal %d SMs x %d "
+                                           "lanes x 2 x %.0f MHz = %.1f TFLOP/s"
+                                           % (fma_peak["scalar_tflops"], fma_peak["packed_tflops"],
+                                              fma_peak["sm_mhz"], sms, FP32_LANES_PER_SM, sm_max, nominal_tflops),
+                             "hbm_frac": hbm[dominant]["frac"], "hbm_peak_gbs": hbm_peak,
+                             "hbm_peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+                             "hbm": hbm,
                              "project_ms_per_launch": pj_ms, "backproject_ms_per_launch": bp_ms},
                 "phase_ms_per_step": {n: float(v / args.steps) for n, v in zip(names, phase_ms)},
                 "cpu_baseline": cpu, "clocks": ck,

@@ -112,10 +112,13 @@ TOMO_API tomo_status tomo_project(tomo_geometry_t g, const float* img, float* si
  * when consecutive angles cannot share an item); larger requests return
  * TOMO_ERR_WORKSPACE with a message and launch nothing. The array (576 KiB)
  * is held on every GPU that loads the library until the process exits.
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture. Every call reuses the same
- * array and leaves its work list there: calls that overlap on the GPU (other
- * streams, or other host threads) race and must be serialized by the caller. */
+ * Every call looks up the array's device address on the current device (the
+ * first lookup may load the library's module on that device) and copies its
+ * work list there from host memory that lives only during the call, so a
+ * stream that is capturing a CUDA graph is refused with TOMO_ERR_INVALID_ARG
+ * and nothing is enqueued. Every call reuses the same array and leaves its
+ * work list there: calls that overlap on the GPU (other streams, or other host
+ * threads) race and must be serialized by the caller. */
 TOMO_API tomo_status tomo_project_noalloc(tomo_geometry_t g, const float* img, float* sino,
                                           const int32_t* angle_idx, int n_sel, int batch,
                                           const float* subtract, tomo_stream_t stream);
@@ -127,6 +130,24 @@ TOMO_API tomo_status tomo_project_noalloc(tomo_geometry_t g, const float* img, f
 TOMO_API tomo_status tomo_backproject(tomo_geometry_t g, const float* sino, float* img,
                              const int32_t* angle_idx, int n_sel, int batch, float beta,
                              tomo_stream_t stream);
+
+/* Work lists of the standalone operator calls. tomo_project, tomo_backproject
+ * and tomo_opnorm_sq need, per (angle selection, batch), the work items of the
+ * persistent kernels and the per-angle constants of the selection. The first
+ * call with a selection builds them on the host and copies them into ONE
+ * device allocation that the geometry keeps; every later call with the same
+ * selection and batch allocates nothing. The geometry keeps at most 256 MiB
+ * and 4096 selections of such lists and drops the least recently used beyond
+ * that (cudaFree, which waits for the device). tomo_geometry_plan builds the
+ * lists of a selection ahead of time (same angle_idx, n_sel and batch rules
+ * as tomo_project; synchronous copy), so that the operator calls that use it
+ * allocate nothing afterwards, e.g. before a stream capture or a loop that
+ * must not allocate. tomo_geometry_cache_stats reports the device
+ * allocations and frees of the geometry's lists so far and the selections
+ * and bytes it holds (each output may be NULL). Neither launches a kernel. */
+TOMO_API tomo_status tomo_geometry_plan(tomo_geometry_t g, const int32_t* angle_idx, int n_sel, int batch);
+TOMO_API tomo_status tomo_geometry_cache_stats(tomo_geometry_t g, int64_t* allocs, int64_t* frees, int64_t* entries,
+                                               int64_t* bytes);
 
 /* Squared spectral norm ||P_sel||_2^2 by `iters` power iterations on
  * P_sel^T P_sel from a seeded start vector. work: device scratch of at least
@@ -155,6 +176,24 @@ TOMO_API tomo_status tomo_sync_status(tomo_geometry_t g, tomo_stream_t stream);
  * The next tomo_sync_status(g) returns TOMO_ERR_TIMEOUT. The projector's
  * own waits give up after one second. */
 TOMO_API tomo_status tomo_selftest_wait(tomo_geometry_t g, int timeout_ms, tomo_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Measurement: the FP32 ceiling of the operators                      */
+/* ------------------------------------------------------------------ */
+
+/* Measured FP32 FMA throughput of the current GPU, the roofline denominator
+ * of the projector and backprojector: both evaluate the system matrix of
+ * Eq. 2 on the fly (Sec. 2.1), so their bound is the FP32 pipe, not memory.
+ * Launches a grid that fills every SM (occupancy API) whose threads run 8
+ * independent chains of dependent FMAs, once with scalar fmaf and once with
+ * packed two-lane FMAs, each timed with CUDA events over one launch of about
+ * target_ms (1..2000) after a warm-up. Outputs (HOST, each may be NULL):
+ * TFLOP/s of the scalar and of the packed form (one FMA = 2 FLOP), and the
+ * SM clock in MHz that the scalar launch ran at (SM cycle counter over the
+ * global nanosecond timer of one thread). Synchronizes the stream; refuses a
+ * stream that is capturing a CUDA graph (TOMO_ERR_INVALID_ARG). */
+TOMO_API tomo_status tomo_fp32_peak(int target_ms, double* tflops_scalar, double* tflops_packed, double* sm_mhz,
+                                    tomo_stream_t stream);
 
 /* ------------------------------------------------------------------ */
 /* Elementwise building blocks of the differentiable unrolled ADMM      */

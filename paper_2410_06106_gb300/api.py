@@ -92,6 +92,9 @@ SIGNATURES = {
     "dadmm_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "dadmm_num_phases": (C.c_int, [C.c_void_p]),
     "dadmm_phase_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "tomo_fp32_peak": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tomo_geometry_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "tomo_geometry_cache_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -130,6 +133,15 @@ def _stream():
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def fp32_peak(target_ms=50):
+    """Measured FP32 FMA throughput of the current GPU (tomo_fp32_peak):
+    {"scalar_tflops", "packed_tflops", "sm_mhz"}"""
+    _require_cuda()
+    v = (C.c_double * 3)()
+    _check(lib().tomo_fp32_peak(int(target_ms), C.byref(v, 0), C.byref(v, 8), C.byref(v, 16), _stream()))
+    return {"scalar_tflops": v[0], "packed_tflops": v[1], "sm_mhz": v[2]}
 
 
 def _host_i32(a):
@@ -208,6 +220,20 @@ class Geometry:
         """raise TomoError if a device-side failure was recorded by an operator
         call on this geometry since the last check (synchronizes the stream)"""
         _check(lib().tomo_sync_status(self.handle, _stream()))
+
+    def plan(self, angle_idx=None, batch=1):
+        """build the work lists of a selection now (tomo_geometry_plan), so that
+        the operator calls that use it allocate no device memory"""
+        _require_cuda()
+        arr, p, n_sel = self._sel(angle_idx)
+        _check(lib().tomo_geometry_plan(self.handle, p, n_sel, int(batch)))
+
+    def cache_stats(self):
+        """{"allocs", "frees", "entries", "bytes"} of the geometry's work-list cache"""
+        v = (C.c_int64 * 4)()
+        _check(lib().tomo_geometry_cache_stats(self.handle, C.byref(v, 0), C.byref(v, 8), C.byref(v, 16),
+                                               C.byref(v, 24)))
+        return {"allocs": v[0], "frees": v[1], "entries": v[2], "bytes": v[3]}
 
     def opnorm_sq(self, angle_idx=None, iters=100, seed=1):
         """||P_sel||^2 by power iteration on the GPU"""

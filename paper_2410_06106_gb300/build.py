@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtomo.so")
-SOURCES = ["operators.cu", "codecs.cu", "dadmm.cu", "noalloc.cu"]
+SOURCES = ["operators.cu", "codecs.cu", "dadmm.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
