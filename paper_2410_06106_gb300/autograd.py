@@ -136,6 +136,8 @@ def unrolled_admm(sino, geom, node_sel, seg_rows, rho, eta1, eta2=0.2, E1=10, E2
         rho = torch.tensor(float(rho), dtype=torch.float64)
     M, N = len(node_sel), geom.N
     dev = sino.device
+    for sel in node_sel:  # every operator call below then runs without device allocation
+        geom.plan(sel, 1)
     d_nodes = [sino.index_select(0, torch.as_tensor(sel, dtype=torch.long, device=dev)) for sel in node_sel]
     u = [torch.zeros(N, N, device=dev, dtype=sino.dtype) for _ in range(M)]
     lam = [torch.zeros(N, N, device=dev, dtype=sino.dtype) for _ in range(M)]

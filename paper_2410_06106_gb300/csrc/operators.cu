@@ -1341,12 +1341,7 @@ tomo_status tomo_geometry_destroy(tomo_geometry_t gh) {
     return guard([&] {
         if (!gh) return;
         Geometry* g = as_geometry(gh);
-        for (auto& s : g->cache) {
-            cudaFree(s.d_angs);
-            cudaFree(s.d_pitems);
-            cudaFree(s.d_bitems);
-            cudaFree(s.d_bk);
-        }
+        for (auto& s : g->cache) cudaFree(s.d_block);
         cudaFree(g->d_ptab);
         cudaFree(g->d_status);
         delete g;
@@ -1356,19 +1351,28 @@ tomo_status tomo_geometry_destroy(tomo_geometry_t gh) {
 }  // extern "C"
 
 namespace tomo {
-// cached work lists of a standalone selection (angle list + batch)
+// cached work lists of a standalone selection (angle list + batch): a hit moves
+// the entry to the most recent end and allocates nothing; a miss builds the
+// lists, copies them into one device allocation and drops least recently used
+// entries beyond the budget
 static Geometry::Sel& selection(Geometry& g, const int32_t* angle_idx, int n_sel, int batch) {
     std::vector<int32_t> key(n_sel);
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)batch;
     for (int q = 0; q < n_sel; ++q) {
         const int a = angle_idx ? angle_idx[q] : q;
         TOMO_REQUIRE(a >= 0 && a < g.A, "angle index " + std::to_string(a) + " out of range");
         key[q] = a;
+        h = (h ^ (uint64_t)(uint32_t)a) * 1099511628211ull;
     }
     std::lock_guard<std::mutex> lk(g.mu);
-    for (auto& s : g.cache)
-        if (s.batch == batch && s.key == key) return s;
+    for (auto it = g.cache.begin(); it != g.cache.end(); ++it)
+        if (it->hash == h && it->batch == batch && it->key == key) {
+            g.cache.splice(g.cache.end(), g.cache, it);
+            return g.cache.back();
+        }
     Geometry::Sel s;
     s.key = key;
+    s.hash = h;
     s.batch = batch;
     std::vector<AngRow> angs(n_sel);
     for (int q = 0; q < n_sel; ++q) angs[q] = AngRow{key[q], q};
@@ -1378,20 +1382,41 @@ static Geometry::Sel& selection(Geometry& g, const int32_t* angle_idx, int n_sel
         build_proj_items(g, angs, 0, n_sel, k, k * n_sel, pi);
         build_bp_items(g, 0, n_sel, k, k * n_sel, 0, 0, bi);
     }
-    s.d_angs = device_upload(angs);
-    s.d_bk = device_upload(bp_list_consts(g, angs));
-    s.d_pitems = device_upload(pi);
-    s.n_pitems = (int)pi.size();
-    s.d_bitems = device_upload(bi);
-    s.n_bitems = (int)bi.size();
-    if (g.cache.size() >= 16) {  // keep the cache small
-        cudaFree(g.cache.front().d_angs);
-        cudaFree(g.cache.front().d_pitems);
-        cudaFree(g.cache.front().d_bitems);
-        cudaFree(g.cache.front().d_bk);
-        g.cache.erase(g.cache.begin());
+    const std::vector<BpConst> bk = bp_list_consts(g, angs);
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t o_angs = 0, o_bk = o_angs + al(sizeof(AngRow) * angs.size());
+    const size_t o_pi = o_bk + al(sizeof(BpConst) * bk.size());
+    const size_t o_bi = o_pi + al(sizeof(ProjItem) * pi.size());
+    s.bytes = o_bi + al(sizeof(BpItem) * bi.size());
+    std::vector<unsigned char> host(s.bytes, 0);
+    std::memcpy(host.data() + o_angs, angs.data(), sizeof(AngRow) * angs.size());
+    std::memcpy(host.data() + o_bk, bk.data(), sizeof(BpConst) * bk.size());
+    if (!pi.empty()) std::memcpy(host.data() + o_pi, pi.data(), sizeof(ProjItem) * pi.size());
+    if (!bi.empty()) std::memcpy(host.data() + o_bi, bi.data(), sizeof(BpItem) * bi.size());
+    while (!g.cache.empty() &&
+           (g.cache_bytes + s.bytes > kSelCacheBytes || g.cache.size() >= kSelCacheEntries)) {
+        cudaFree(g.cache.front().d_block);
+        g.cache_bytes -= g.cache.front().bytes;
+        ++g.list_frees;
+        g.cache.pop_front();
     }
-    g.cache.push_back(s);
+    TOMO_CUDA(cudaMalloc(&s.d_block, s.bytes));
+    ++g.list_allocs;
+    const cudaError_t e = cudaMemcpy(s.d_block, host.data(), s.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(s.d_block);
+        ++g.list_frees;
+        fail(TOMO_ERR_CUDA, std::string("work-list upload: ") + cudaGetErrorString(e));
+    }
+    unsigned char* base = static_cast<unsigned char*>(s.d_block);
+    s.d_angs = reinterpret_cast<AngRow*>(base + o_angs);
+    s.d_bk = reinterpret_cast<BpConst*>(base + o_bk);
+    s.d_pitems = pi.empty() ? nullptr : reinterpret_cast<ProjItem*>(base + o_pi);
+    s.n_pitems = (int)pi.size();
+    s.d_bitems = bi.empty() ? nullptr : reinterpret_cast<BpItem*>(base + o_bi);
+    s.n_bitems = (int)bi.size();
+    g.cache_bytes += s.bytes;
+    g.cache.push_back(std::move(s));
     return g.cache.back();
 }
 }  // namespace tomo
@@ -1450,6 +1475,29 @@ tomo_status tomo_backproject(tomo_geometry_t gh, const float* sino, float* img, 
         p.prescaled = 0;
         p.beta = beta;
         launch_backproject_store(p, s.n_bitems, (cudaStream_t)stream);
+    });
+}
+
+tomo_status tomo_geometry_plan(tomo_geometry_t gh, const int32_t* angle_idx, int n_sel, int batch) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        check_device(*g);
+        TOMO_REQUIRE(batch >= 1, "batch must be >= 1");
+        TOMO_REQUIRE(n_sel >= 1 && n_sel <= 65536, "n_sel out of range");
+        TOMO_REQUIRE(angle_idx || n_sel == g->A, "angle_idx NULL requires n_sel == n_angles");
+        selection(*g, angle_idx, n_sel, batch);
+    });
+}
+
+tomo_status tomo_geometry_cache_stats(tomo_geometry_t gh, int64_t* allocs, int64_t* frees, int64_t* entries,
+                                      int64_t* bytes) {
+    return guard([&] {
+        Geometry* g = as_geometry(gh);
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (allocs) *allocs = g->list_allocs;
+        if (frees) *frees = g->list_frees;
+        if (entries) *entries = (int64_t)g->cache.size();
+        if (bytes) *bytes = (int64_t)g->cache_bytes;
     });
 }
 

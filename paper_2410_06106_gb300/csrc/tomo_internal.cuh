@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <list>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -157,10 +158,15 @@ struct Geometry {
     std::vector<BpConst> hb;      // [A] backprojector constants (host; lists copy from here)
     int* d_status = nullptr;  // device status word of standalone operator calls (bit 4: a wait gave up)
     std::vector<double> c, s;
-    // cached device work lists of standalone project/backproject calls
+    // cached device work lists of standalone project/backproject calls: one device
+    // allocation per (angle selection, batch), kept until the budget below forces
+    // the least recently used out, so repeated calls allocate nothing
     struct Sel {
         std::vector<int32_t> key;
+        uint64_t hash = 0;
         int batch = 0;
+        void* d_block = nullptr;  // the four lists below, 256-byte aligned inside one allocation
+        size_t bytes = 0;
         AngRow* d_angs = nullptr;
         BpConst* d_bk = nullptr;  // backprojector constants of the selection, in its order
         ProjItem* d_pitems = nullptr;
@@ -168,9 +174,13 @@ struct Geometry {
         BpItem* d_bitems = nullptr;
         int n_bitems = 0;
     };
-    std::vector<Sel> cache;
+    std::list<Sel> cache;  // most recently used last
+    size_t cache_bytes = 0;
+    long long list_allocs = 0, list_frees = 0;
     std::mutex mu;
 };
+constexpr size_t kSelCacheBytes = size_t(256) << 20;  // device bytes of cached work lists per geometry
+constexpr size_t kSelCacheEntries = 4096;             // cached selections per geometry
 
 // host: true when the rows of the image are the major (iteration) axis of
 // rays at this angle, i.e. |cos| >= |sin| (same test as the device)

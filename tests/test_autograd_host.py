@@ -26,6 +26,9 @@ class DenseGeom:
     def backproject(self, sino, sel=None):
         return torch.from_numpy(self.og.backproject(sino.detach().numpy(), sel))
 
+    def plan(self, sel=None, batch=1):
+        self.planned = getattr(self, "planned", 0) + 1
+
 
 @pytest.fixture
 def cpu_kernels(monkeypatch):

@@ -2,8 +2,10 @@
 matched backprojection kernel) and the unrolled 10-iteration unquantized
 dADMM, differentiated with respect to rho and the sinogram with one
 checkpoint per iteration. Checked against central finite differences of the
-FP64 oracle (small problem) and of the GPU forward (full 1024^2 size), and
-against the oracle's adjoint."""
+FP64 oracle (computed live on the small problem, stored by
+tests/golden/make_trajectory_goldens.py at the full 1024^2 size) and of the
+GPU forward (the sinogram direction, where the map is linear), and against
+the oracle's adjoint."""
 import numpy as np
 import pytest
 import torch
@@ -98,30 +100,32 @@ def test_unrolled_admm_gradients_match_oracle_finite_differences():
 
 def test_unrolled_admm_full_size_checkpointed():
     """1024^2, 1440 angles, 8 nodes (interleaved, complete graph), 10 unrolled
-    iterations. Checkpointing (one per iteration) changes no gradient and
-    keeps the peak memory well below the stored-activation run; the sinogram
-    gradient matches central differences of the GPU forward (the map is
-    linear in d, so they are exact up to FP32 rounding); the rho gradient
-    matches them to the FP32 forward's noise (the 1e-3 check of the rho
-    gradient against the FP64 oracle runs on the small problem above)"""
+    iterations with the oracle's step sizes. Checkpointing (one per iteration)
+    changes no gradient and keeps the peak memory well below the
+    stored-activation run; the forward loss <w, x_10> and dL/drho (eta1 held
+    fixed) match the FP64 oracle's value and central difference stored by
+    tests/golden/make_trajectory_goldens.py within 1e-3; the sinogram gradient
+    matches central differences of the GPU forward (the map is linear in d,
+    so they are exact up to FP32 rounding)"""
     need_gpu()
+    import os
+    z = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c4_diff_trajectory.npz"))
     prob = synth.make_problem("c4_diff")
     gd = prob["geometry"]
     g = api.Geometry(gd["N"], gd["B"], gd["theta"])
     ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
     sel = [idx[ptr[m]:ptr[m + 1]] for m in range(prob["M"])]
-    L = np.array([g.opnorm_sq(s, iters=20) for s in sel])
-    eta = 1.0 / (L + 1.0)
-    rng = np.random.default_rng(5)
-    w = cuda(rng.standard_normal((gd["N"], gd["N"])))
+    eta = z["eta1"]
+    w_host = np.random.default_rng(int(z["w_seed"])).standard_normal((gd["N"], gd["N"]))
+    w = torch.as_tensor(w_host).cuda()  # float64
     sino = cuda(prob["sino"][0])
 
     def loss_of(rho_val, d, grad=False, checkpoint=True):
         rho = torch.tensor(rho_val, dtype=torch.float64, requires_grad=grad)
         x = autograd.unrolled_admm(d, g, sel, prob["seg_row_ptr"], rho, eta, iters=10, checkpoint=checkpoint)
-        return torch.sum(x.double() * w.double()), rho
+        return torch.sum(x.double() * w), rho
 
-    grads, peaks = [], []
+    grads, peaks, losses = [], [], []
     for ck in (True, False):
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats()
@@ -132,17 +136,51 @@ def test_unrolled_admm_full_size_checkpointed():
         torch.cuda.synchronize()
         peaks.append(torch.cuda.max_memory_allocated() - base)
         grads.append((rho.grad.item(), d.grad.detach().clone()))
+        losses.append(loss.item())
         del loss, rho, d
     assert grads[0][0] == grads[1][0] and torch.equal(grads[0][1], grads[1][1])
     assert peaks[0] < 0.25 * peaks[1], peaks
     g_rho, g_d = grads[0]
+    # forward and rho-derivative against the FP64 oracle
+    assert abs(losses[0] - float(z["loss"])) <= 1e-3 * abs(float(z["loss"])), (losses[0], float(z["loss"]))
+    h = float(z["h"])  # rho (1 +- h) with rho = 1
+    fd64 = (float(z["loss_plus"]) - float(z["loss_minus"])) / (2.0 * h)
+    print("dL/drho: autograd %.9e, FP64 oracle central difference %.9e, rel %.3e"
+          % (g_rho, fd64, abs(g_rho - fd64) / abs(fd64)))
+    assert abs(g_rho - fd64) <= 1e-3 * abs(fd64), (g_rho, fd64)
     v = torch.randn(sino.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     with torch.no_grad():
         fdd = (loss_of(1.0, sino + v)[0] - loss_of(1.0, sino - v)[0]).item() / 2
     add = float(torch.sum(g_d.double() * v.double()))
     assert abs(add - fdd) <= 1e-3 * abs(fdd), (add, fdd)
-    h = 0.05
-    with torch.no_grad():
-        fd = (loss_of(1.0 + h, sino)[0] - loss_of(1.0 - h, sino)[0]).item() / (2 * h)
-    assert abs(g_rho - fd) <= 2e-2 * abs(fd), (g_rho, fd)
+    g.close()
+
+
+def test_unrolled_admm_with_64_nodes_allocates_no_work_lists_after_setup():
+    """64 nodes: the unrolled iteration plans its 64 angle selections once
+    (one device allocation each) and then runs every projector and
+    backprojector call of two further forward and backward passes without
+    a device allocation or free of the library's work lists"""
+    need_gpu()
+    N, A, B, M = 32, 128, 47, 64
+    p = small_problem(N=N, A=A, B=B, M=M, graph="complete", part="interleaved", noise=0.01, seed=2,
+                      E1=2, E2=2)
+    g = api.Geometry(N, B, p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    sel = [idx[ptr[m]:ptr[m + 1]] for m in range(M)]
+    eta = np.full(M, 1e-3)
+    d = cuda(p["sino"][0]).requires_grad_(True)
+
+    def run():
+        rho = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        x = autograd.unrolled_admm(d, g, sel, p["seg_row_ptr"], rho, eta, E1=2, E2=2, iters=2)
+        x.sum().backward()
+        torch.cuda.synchronize()
+        return rho.grad.item()
+
+    g0 = run()
+    after_setup = g.cache_stats()
+    assert after_setup["allocs"] == M and after_setup["frees"] == 0 and after_setup["entries"] == M
+    assert run() == g0 and run() == g0  # deterministic, and no new lists
+    assert g.cache_stats() == after_setup
     g.close()
