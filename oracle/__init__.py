@@ -33,6 +33,7 @@ def lib():
             "orc_project_rays": (None, [i32, i32, p, p, i32, p, p, p, p]),
             "orc_backproject_pixels": (None, [i32, i32, p, p, i32, p, p, i32, p, p]),
             "orc_opnorm_sq": (d, [i32, i32, p, p, i32, p, i32, u64]),
+            "orc_alg2_node": (d, [i32, i32, p, p, i32, p, p, p, p, d, d, i32, p]),
             "orc_mix64": (u64, [u64]),
             "orc_kmeans_key": (u64, [u64, i32, i32, i32]),
             "orc_kmeans": (None, [p, i64, i32, i32, u64, p, p, p, p]),
@@ -141,6 +142,16 @@ class Geometry:
         lib().orc_backproject_pixels(self.N, self.B, _ptr(self.c), _ptr(self.s), len(sel),
                                      _ptr(sel), _ptr(sino), len(px), _ptr(px), _ptr(out))
         return out
+
+    def alg2_node(self, u, xview, lam, sino, aidx, rho, eta1, E1):
+        """Algorithm 2 for one node (E1 steps from u, view and dual fixed):
+        returns (u after the steps, residual norm^2 at the last step)"""
+        uu = _f64(u).copy()
+        sel = _i32(aidx)
+        res = lib().orc_alg2_node(self.N, self.B, _ptr(self.c), _ptr(self.s), len(sel), _ptr(sel),
+                                  _ptr(_f64(sino)), _ptr(_f64(xview)), _ptr(_f64(lam)), float(rho),
+                                  float(eta1), int(E1), _ptr(uu))
+        return uu, res
 
     def opnorm_sq(self, aidx=None, iters=100, seed=1):
         sel = self._sel(aidx)

@@ -726,6 +726,44 @@ static void build_view(const view_ctx* v, int slice, int m, int k, const int32_t
     }
 }
 
+/* Algorithm 2 for one node: E1 gradient steps u <- u - eta1 Delta with
+ * Delta = P_m^T (P_m u - d_m) + rho (u - (x_m - lambda_m / rho)), the node's
+ * view x_m and dual lambda_m held fixed (warm start from the u given).
+ * d_sl [A][B] is the slice's whole sinogram (rows ang[0..na) are d_m);
+ * r [na][B] and g [N][N] are scratch. Returns ||P_m u - d_m||^2 at the last
+ * step (0 when E1 = 0). */
+static double alg2_steps(int N, int B, const double* c, const double* s, int na, const int32_t* ang,
+                         const double* d_sl, const double* xv, const double* lm, double rho,
+                         double eta1, int E1, double* um, double* r, double* g) {
+    const long n = (long)N * N;
+    double resid2 = 0.0;
+    for (int e = 0; e < E1; ++e) {
+        orc_project(N, B, c, s, na, ang, 1, um, r); /* P_m u_m */
+        for (int q = 0; q < na; ++q)
+            for (int b = 0; b < B; ++b)
+                r[(long)q * B + b] -= d_sl[(long)ang[q] * B + b]; /* - d_m */
+        if (e == E1 - 1)
+            for (long i = 0; i < (long)na * B; ++i) resid2 += r[i] * r[i];
+        orc_backproject(N, B, c, s, na, ang, 1, r, g); /* P_m^T (P_m u_m - d_m) */
+        for (long i = 0; i < n; ++i) {
+            double delta = g[i] + rho * (um[i] - (xv[i] - lm[i] / rho));
+            um[i] -= eta1 * delta;
+        }
+    }
+    return resid2;
+}
+
+double orc_alg2_node(int N, int B, const double* c, const double* s, int na, const int32_t* ang,
+                     const double* sino_slice, const double* xview, const double* lam, double rho,
+                     double eta1, int E1, double* u) {
+    double* r = (double*)malloc(sizeof(double) * (na > 0 ? (long)na * B : 1));
+    double* g = (double*)malloc(sizeof(double) * (long)N * N);
+    const double res = alg2_steps(N, B, c, s, na, ang, sino_slice, xview, lam, rho, eta1, E1, u, r, g);
+    free(r);
+    free(g);
+    return res;
+}
+
 int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       const double* c, const double* s,
                       const int32_t* node_ang_ptr, const int32_t* node_ang,
@@ -790,23 +828,11 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
         /* Algorithm 2 on every node: u_m <- u_m - eta1 Delta, E1 times */
         for (int m = 0; m < M; ++m) {
             double* um = u + ((long)sl * M + m) * n;
-            double* lm = lam + ((long)sl * M + m) * n;
+            const double* lm = lam + ((long)sl * M + m) * n;
             const int na = node_ang_ptr[m + 1] - node_ang_ptr[m];
             const int32_t* ang = node_ang + node_ang_ptr[m];
             build_view(&vc, sl, m, k, held, xv); /* x_m^k */
-            for (int e = 0; e < E1; ++e) {
-                orc_project(N, B, c, s, na, ang, 1, um, r); /* P_m u_m */
-                for (int q = 0; q < na; ++q)
-                    for (int b = 0; b < B; ++b)
-                        r[(long)q * B + b] -= d_sl[(long)ang[q] * B + b]; /* - d_m */
-                if (e == E1 - 1)
-                    for (long i = 0; i < (long)na * B; ++i) resid2 += r[i] * r[i];
-                orc_backproject(N, B, c, s, na, ang, 1, r, g); /* P_m^T (P_m u_m - d_m) */
-                for (long i = 0; i < n; ++i) {
-                    double delta = g[i] + rho * (um[i] - (xv[i] - lm[i] / rho));
-                    um[i] -= eta1[m] * delta;
-                }
-            }
+            resid2 += alg2_steps(N, B, c, s, na, ang, d_sl, xv, lm, rho, eta1[m], E1, um, r, g);
         }
 
         /* Algorithm 3 on every owner's segment, then its messages (Eq. 23) */

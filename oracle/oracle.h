@@ -57,6 +57,16 @@ void orc_backproject_pixels(int N, int B, const double* c, const double* s,
                             int nsel, const int32_t* aidx, const double* sino,
                             int npix, const int32_t* pix, double* out);
 
+/* Algorithm 2 for a single node m: E1 steps of
+ *   u <- u - eta1 (P_m^T (P_m u - d_m) + rho (u - (x_m - lambda_m / rho)))
+ * from the u given (in place), with the node's view x_m (xview) and dual
+ * lambda_m (lam) held fixed. ang[0..na) are the node's angle indices,
+ * sino_slice [A][B] the slice's sinogram (rows ang[q] are d_m). All images
+ * [N][N]. Returns ||P_m u - d_m||^2 at the last step (0 if E1 = 0). */
+double orc_alg2_node(int N, int B, const double* c, const double* s, int na, const int32_t* ang,
+                     const double* sino_slice, const double* xview, const double* lam, double rho,
+                     double eta1, int E1, double* u);
+
 /* ||P_sel||_2^2 by power iteration on P^T P from a seeded start vector */
 double orc_opnorm_sq(int N, int B, const double* c, const double* s, int nsel,
                      const int32_t* aidx, int iters, uint64_t seed);

@@ -5,10 +5,9 @@ against the FP64 oracle.
 one iteration; the GPU's iterate k+1 must match (u, lambda, x segments:
 relative L2 <= 1e-5; quantized messages: levels identical except at
 rounding ties);
-(ii) full trajectories: relative L2 <= 1e-3 after the stated iterations, of
-the reconstruction for the unquantized shape and of the continuous iterate u
-for the quantized ones (their dequantized messages are discontinuous in the
-iterate and drift; the drift is measured and printed);
+(ii) the tiny shape's full trajectory: the reconstruction within 1e-3 after
+its 50 iterations (the other shapes' trajectories, against stored oracle
+runs, are in test_gpu_trajectories.py);
 plus: the batched (persistent, graph-captured) and plain (per-node launch)
 forms are bit-identical, and a checkpoint resumes bit-identically."""
 import numpy as np
@@ -72,9 +71,20 @@ def test_state_injection_small(quant, graph, M):
     o.load_state(*before)
     ost = o.iterate(p["sino"])
     compare_states(after, o, p)
-    # bytes on the wire: exact sizes (K-means, identity) and entropy-coded JPEG messages,
-    # which a code at a rounding tie may change by a few bits
-    assert abs(st[0, :, 4] - ost[:, 4]).max() <= 1e-3 * ost[:, 4].max()
+    compare_stats(st[0], ost, quant != "none")
+
+
+def compare_stats(st, ost, quantized):
+    """all five FP64 statistics [S, 5] of one iteration: the residual norm and
+    node 0's previous view norm come from continuous state (1e-5); the gap and
+    change norms also see the new messages, which at a rounding tie differ by
+    one quantization level (1e-5 unquantized, 1e-3 quantized); bytes: exact
+    sizes (K-means, identity) and entropy-coded JPEG messages, which a code at
+    a rounding tie may change by a few bits"""
+    tol_msg = 1e-3 if quantized else 1e-5
+    for j, tol in ((0, tol_msg), (1, tol_msg), (2, 1e-5), (3, 1e-5)):
+        assert rel_l2(st[:, j], ost[:, j]) <= tol, (j, st[:, j], ost[:, j])
+    assert abs(st[:, 4] - ost[:, 4]).max() <= 1e-3 * ost[:, 4].max()
 
 
 @pytest.mark.parametrize("name", ["c2_kmeans", "c3_batch_jpeg"])
@@ -90,12 +100,13 @@ def test_state_injection_full_config(name):
     sino = torch.as_tensor(p["sino"]).cuda()
     s.step(sino, 3)
     before = gpu_state(s)
-    s.step(sino, 1)
+    st = s.step(sino, 1)
     after = gpu_state(s)
     o = O.DADMM(p, eta)
     o.load_state(*before)
-    o.iterate(p["sino"])
+    ost = o.iterate(p["sino"])
     compare_states(after, o, p)
+    compare_stats(st[0], ost, True)
 
 
 def test_c1_trajectory_matches_oracle():
@@ -111,32 +122,6 @@ def test_c1_trajectory_matches_oracle():
     ost = np.stack(ost)
     assert rel_l2(st[:, :, 0], ost[:, :, 0]) <= 1e-3  # primal gap trajectory
     assert np.all(st[:, :, 4] == ost[:, :, 4])        # bytes on the wire
-
-
-@pytest.mark.parametrize("name,iters", [("c2_kmeans", 30), ("c3_batch_jpeg", 12)])
-def test_quantized_trajectory_matches_oracle(name, iters):
-    """full trajectories of the quantized shapes (K-means messages on a ring,
-    c2; JPEG messages on a random geometric graph with uneven nodes, c3).
-    The continuous iterate u stays within the protocol's 1e-3 of the oracle's.
-    The dequantized messages do not: K-means and JPEG decisions are
-    discontinuous, so the ~1e-7 differences between the FP32 and FP64 states
-    move a few decisions (and Lloyd's centroids) from the second iteration
-    on, and the owners' reconstruction drifts (measured: 5e-2 after 12
-    iterations of c3, 1.6e-1 after 30 of c2). That drift is printed, not
-    asserted; one-iteration parity of the messages is the state-injection
-    tests' job"""
-    need_gpu()
-    p = synth.make_problem(name)
-    eta = oracle_eta1(p, iters=60)
-    s = api.DADMM(p, eta)
-    s.step(torch.as_tensor(p["sino"]).cuda(), iters)
-    o = O.DADMM(p, eta)
-    for _ in range(iters):
-        o.iterate(p["sino"])
-    err_u = rel_l2(s.u.cpu().numpy(), o.u)
-    err_x = rel_l2(s.home_view().cpu().numpy(), o.home_view())
-    print("%s: %d iterations, rel-L2 of u %.3e, of the quantized reconstruction %.3e" % (name, iters, err_u, err_x))
-    assert err_u <= 1e-3
 
 
 @pytest.mark.parametrize("quant", ["none", "alternate"])
@@ -171,11 +156,12 @@ def test_launch_shapes_follow_the_oracle(tune, shape):
     sino = torch.as_tensor(p["sino"]).cuda()
     s.step(sino, 2)
     before = gpu_state(s)
-    s.step(sino, 1)
+    st = s.step(sino, 1)
     o = O.DADMM(p, eta)
     o.load_state(*before)
-    o.iterate(p["sino"])
+    ost = o.iterate(p["sino"])
     compare_states(gpu_state(s), o, p)
+    compare_stats(st[0], ost, True)
     assert s.launch_shape() == shape
 
 
@@ -308,3 +294,54 @@ def test_stress_config_sampled_parity():
         delta = og.backproject_pixels(res, q, angs) + 2.0 * lam1[sl, m]
         got = (u1[sl, m].ravel()[q] - s.u[sl, m].cpu().numpy().ravel()[q].astype(np.float64)) / eta[m]
         assert rel_l2(got, delta) <= 1e-4, (sl, m)
+
+
+def node_view(hist, k, D, sl, m, p, dist, first):
+    """node m's view x_m^k of slice sl, assembled from the GPU's message ring by
+    the relay rule: segment s holds the message of iteration k - max(dist - 1, 0),
+    in the plane of the path's first edge (the home plane for the node's own
+    segment), zero before the first message arrives"""
+    N, M, seg = p["geometry"]["N"], p["M"], p["seg_row_ptr"]
+    out = np.zeros((N, N))
+    for s in range(M):
+        lag = 0 if s == m else dist[s, m] - 1
+        ver = k - lag
+        if ver < 1:
+            continue
+        kind = p["home_q"][m] if s == m else p["edge_q"][s, first[s, m]]
+        out[seg[s]:seg[s + 1]] = hist[ver % D, kind, sl, seg[s]:seg[s + 1]].cpu().numpy()
+    return out
+
+
+def test_stress_config_inner_loop_by_state_injection():
+    """the 8 x 2048^2, 64-node problem with the benchmark's E1 = 10 inner steps,
+    in the launch configuration the benchmark times (batched, auto-tuned
+    shapes): after two iterations, the GPU's u_m of the third iteration equals
+    the oracle's Algorithm 2 (ten steps, whole 2048^2 image) from the GPU's
+    u_m, lambda_m and the node's view of x (assembled from the message ring)
+    for four (slice, node) pairs, at the state-injection tolerance 1e-5"""
+    need_gpu()
+    p = synth.make_problem("c5_stress")
+    N, B, rho, E1 = p["geometry"]["N"], p["geometry"]["B"], p["rho"], p["E1"]
+    assert E1 == 10
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    eta = 1.0 / (1.2 * np.diff(ptr) * N + rho)  # any step: both sides get the same
+    og = O.Geometry(N, B, p["geometry"]["theta"])
+    dist, first = O.relay_tables(p["adj"])
+    s = api.DADMM(p, eta)
+    sino = torch.as_tensor(p["sino"]).cuda()
+    s.step(sino, 2, stats=False)
+    k = int(s.iter.item())
+    D = s.hist.shape[0]
+    picks = [(0, 0), (2, 9), (5, 42), (7, 63)]
+    before = {}
+    for sl, m in picks:
+        before[sl, m] = (s.u[sl, m].cpu().numpy(), s.lam[sl, m].cpu().numpy(),
+                         node_view(s.hist, k, D, sl, m, p, dist, first))
+    s.step(sino, 1, stats=False)
+    for sl, m in picks:
+        u0, l0, xv = before[sl, m]
+        want, _ = og.alg2_node(u0, xv, l0, p["sino"][sl], idx[ptr[m]:ptr[m + 1]], rho, eta[m], E1)
+        err = rel_l2(s.u[sl, m].cpu().numpy(), want)
+        assert err <= 1e-5, (sl, m, err)
+    del s

@@ -286,3 +286,29 @@ def test_change_statistic_over_the_first_two_iterations():
     assert np.isclose(s1[0, 1], np.sum(x1 * x1), rtol=1e-13, atol=0)
     assert np.isclose(s2[0, 2], np.sum(x1 * x1), rtol=1e-13, atol=0)
     assert np.isclose(s2[0, 1], np.sum((x2 - x1) ** 2), rtol=1e-12, atol=0)
+
+
+def test_single_node_algorithm2_solves_its_subproblem_and_matches_the_iteration():
+    """orc_alg2_node (Algorithm 2 for one node, used to check single nodes of
+    problems too large for the whole oracle iteration): with many steps it
+    solves Eq. 15, P_m^T (P_m u - d_m) + rho (u - x_m) + lambda_m = 0; with
+    E1 = 4 it reproduces node m's u of the full iteration bit for bit"""
+    N, B, A, M, rho = 8, 13, 16, 3, 1.5
+    p = small_problem(N=N, A=A, B=B, M=M, graph="complete", E1=4, noise=0.05, seed=7, rho=rho)
+    eta = oracle_eta1(p)
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    ptr, idx = p["node_ang_ptr"], p["node_ang"]
+    rng = np.random.default_rng(12)
+    u0, lam0 = rng.random((1, M, N, N)), rng.standard_normal((1, M, N, N))
+    xk = rng.random((N, N))
+    st = O.DADMM(p, eta)
+    st.load_state(u0, lam0, rng.random((1, N, N)), np.broadcast_to(xk, (st.D, 3, 1, N, N)), 3)
+    st.iterate(p["sino"])
+    d = p["sino"][0].astype(np.float64)
+    for m in range(M):
+        sel = idx[ptr[m]:ptr[m + 1]]
+        um, _ = geo.alg2_node(u0[0, m], xk, lam0[0, m], d, sel, rho, eta[m], 4)
+        assert np.array_equal(um, st.u[0, m])
+        us, _ = geo.alg2_node(u0[0, m], xk, lam0[0, m], d, sel, rho, eta[m], 3000)
+        grad = geo.backproject(geo.project(us, sel) - d[sel], sel) + rho * (us - xk) + lam0[0, m]
+        assert np.abs(grad).max() < 1e-9 * np.abs(lam0).max()
