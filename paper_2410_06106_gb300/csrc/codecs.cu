@@ -1,8 +1,9 @@
 // Message quantizers of dADMM-K and dADMM-J (Sec. 2.7) on GB300:
 //   - scalar K-means (Algorithm 5): one CTA per vector, warp-parallel seeded
-//     initialisation, FP32 nearest-centre decisions, FP64 centroid sums kept
-//     per thread in shared memory and combined with warp shuffles in a fixed
-//     order (deterministic);
+//     initialisation, FP32 nearest-centre decisions by binary search over the
+//     sorted centres, exact 64-bit fixed-point centroid sums kept per thread
+//     in shared memory and combined with warp shuffles (order-independent,
+//     so deterministic), means in FP64;
 //   - JPEG-style codec: one thread per 8x8 block, the orthonormal DCT-II and
 //     its inverse separable in registers on the FP32 cores, luminance table
 //     of ITU-T T.81 Annex K scaled by the IJG quality rule.
@@ -26,11 +27,35 @@ size_t kmeans_smem(int kmax) {
            32 * sizeof(double);
 }
 
+// Nearest centre by FP32 distance |v - c_j| with ties to the lower index, over
+// centres sorted ascending (s_cent, padded with +inf up to KMAX). The computed
+// distance fl(v - c_j) of the centres at or below v falls (weakly) as j grows
+// and fl(c_j - v) of those above v rises, because rounding is monotone; so
+// with p = #{j : c_j <= v} (a branch-free binary search) the nearest centre is
+// p - 1 or p, and among equal distances on the left the lowest index is found
+// by walking down a run of equal values (only duplicate centres, or centres
+// closer together than the rounding of v - c, make that run longer than 1).
+template <int KMAX>
+__device__ __forceinline__ int nearest_centre(const float* s_cent, int k, float v) {
+    int p = 0;
+#pragma unroll
+    for (int step = KMAX / 2; step >= 1; step >>= 1)
+        if (s_cent[p + step - 1] <= v) p += step;
+    if (s_cent[p] <= v) ++p;
+    p = min(p, k);  // the +inf padding counts only for v = +inf
+    if (p == 0) return 0;
+    const float dl = v - s_cent[p - 1];
+    if (p < k && s_cent[p] - v < dl) return p;  // strict: a tie stays with the lower index
+    int best = p - 1;
+    while (best > 0 && v - s_cent[best - 1] == dl) --best;
+    return best;
+}
+
 template <int KMAX>
 __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, int iters, uint64_t key,
                              uint8_t* codes, float* cent_out, float* deq, double* obj) {
     extern __shared__ __align__(16) unsigned char km_smem[];
-    double* s_sum = reinterpret_cast<double*>(km_smem);               // [KMAX][256]
+    long long* s_sum = reinterpret_cast<long long*>(km_smem);           // [KMAX][256] fixed-point member sums
     int* s_cnt = reinterpret_cast<int*>(s_sum + KMAX * kKmThreads);    // [KMAX][256]
     float* s_cent = reinterpret_cast<float*>(s_cnt + KMAX * kKmThreads);
     // 32 doubles after the centres: byte offset KMAX * (256 * 12 + 4), a multiple of 8
@@ -38,6 +63,17 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned full = 0xffffffffu;
     const uint64_t un = (uint64_t)n;
+
+    // Member sums are exact 64-bit fixed-point sums, scale 2^sh with
+    // |v| 2^sh < 2^(62 - lg n) for every value, so that n of them fit: exact and
+    // independent of the summation order. The scaled value v 2^sh is exact in
+    // FP32 (a power-of-two scale); only its fraction below 2^0, i.e. below
+    // 2^(lg n - 62) max|v|, is rounded away.
+    float amax = 0.f;
+    for (long long i = tid; i < n; i += kKmThreads) amax = fmaxf(amax, fabsf(in[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(full, amax, o));
+    if (lane == 0) reinterpret_cast<float*>(s_red)[warp] = amax;
 
     // initial centres: value at a seeded index, moving to the next index while
     // the value is already a centre (64 probes at most, checked 32 at a time)
@@ -58,7 +94,7 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
             if (lane == 0) s_cent[j] = pick;
             __syncwarp();
         }
-        if (lane == 0)
+        if (lane == 0) {
             for (int j = 1; j < k; ++j) {  // ascending order
                 const float t = s_cent[j];
                 int q = j - 1;
@@ -68,42 +104,39 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
                 }
                 s_cent[q + 1] = t;
             }
+            for (int j = k; j < KMAX; ++j) s_cent[j] = INFINITY;
+        }
     }
     __syncthreads();
+    for (int w = 0; w < kKmThreads / 32; ++w) amax = fmaxf(amax, reinterpret_cast<const float*>(s_red)[w]);
+    int lgn = 0;
+    while (lgn < 62 && (1ll << lgn) < n) ++lgn;
+    const int e = ((__float_as_int(amax) >> 23) & 0xff) - 126;  // amax < 2^e (e = -126 for amax = 0)
+    const int sh = max(-126, min(127, 62 - lgn - e));
+    const float scale = __int_as_float((sh + 127) << 23);
+    __syncthreads();  // s_red is reused below
 
     for (int t = 0; t <= iters; ++t) {
         const bool last = (t == iters);
-        float cr[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) cr[j] = j < k ? s_cent[j] : INFINITY;
         if (!last)
             for (int j = 0; j < k; ++j) {
-                s_sum[j * kKmThreads + tid] = 0.0;
+                s_sum[j * kKmThreads + tid] = 0;
                 s_cnt[j * kKmThreads + tid] = 0;
             }
         double J = 0.0;
         for (long long i = tid; i < n; i += kKmThreads) {
             const float v = in[i];
-            int best = 0;
-            float bd = fabsf(v - cr[0]);
-#pragma unroll
-            for (int j = 1; j < KMAX; ++j) {
-                const float d = fabsf(v - cr[j]);
-                if (d < bd) {  // strict: ties stay with the lower index
-                    bd = d;
-                    best = j;
-                }
-            }
+            const int best = nearest_centre<KMAX>(s_cent, k, v);
             if (last) {
                 if (codes) codes[i] = (uint8_t)best;
                 deq[i] = s_cent[best];
             } else {
-                s_sum[best * kKmThreads + tid] += (double)v;
+                s_sum[best * kKmThreads + tid] += __float2ll_rn(v * scale);
                 s_cnt[best * kKmThreads + tid] += 1;
             }
             if (obj) {
-                const double e = (double)v - (double)s_cent[best];
-                J += e * e;
+                const double d = (double)v - (double)s_cent[best];
+                J += d * d;
             }
         }
         if (obj) {
@@ -119,9 +152,9 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
         }
         if (last) break;
         __syncthreads();
-        // centre update: member sums in a fixed order (8 per lane, then a shuffle tree)
+        // centre update: the exact member sum over the threads' slots, mean in FP64
         for (int j = warp; j < k; j += kKmThreads / 32) {
-            double sm = 0.0;
+            long long sm = 0;
             int c = 0;
 #pragma unroll
             for (int r = 0; r < kKmThreads / 32; ++r) {
@@ -133,7 +166,7 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
                 sm += __shfl_xor_sync(full, sm, o);
                 c += __shfl_xor_sync(full, c, o);
             }
-            if (lane == 0 && c > 0) s_cent[j] = (float)(sm / (double)c);
+            if (lane == 0 && c > 0) s_cent[j] = (float)ldexp((double)sm / (double)c, -sh);
         }
         __syncthreads();
     }
@@ -642,10 +675,14 @@ __device__ __forceinline__ void put_bits(uint32_t* buf, unsigned long long o, ui
     if ((uint32_t)x) atomicOr(buf + (o >> 5) + 1, (uint32_t)x);
 }
 
-// CTA-wide exclusive scan of one value per thread (256 threads); returns the
+// threads of the entropy coder's CTA: each codes one 8 x 8 block per round, so a
+// segment of 1024 blocks takes 4 rounds
+constexpr int kEntThreads = 256;
+
+// CTA-wide exclusive scan of one value per thread (kEntThreads threads); returns the
 // prefix and sets *total
 __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* total) {
-    __shared__ long long s_w[kJpegThreads / 32];
+    __shared__ long long s_w[kEntThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long x = v;
 #pragma unroll
@@ -656,7 +693,7 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* 
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     long long before = 0, all = 0;
-    for (int w = 0; w < kJpegThreads / 32; ++w) {
+    for (int w = 0; w < kEntThreads / 32; ++w) {
         if (w < warp) before += s_w[w];
         all += s_w[w];
     }
@@ -665,12 +702,12 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* 
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(kJpegThreads) jpeg_entropy_kernel(const __grid_constant__ EntropyParams p) {
+__global__ void __launch_bounds__(kEntThreads) jpeg_entropy_kernel(const __grid_constant__ EntropyParams p) {
     __shared__ uint32_t s_dc[12], s_ac[256];
     __shared__ uint8_t s_zz[64];
     __shared__ int s_bad;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 256; i += kJpegThreads) s_ac[i] = p.t.ac[i];
+    for (int i = tid; i < 256; i += kEntThreads) s_ac[i] = p.t.ac[i];
     if (tid < 12) s_dc[tid] = p.t.dc[tid];
     if (tid < 64) s_zz[tid] = p.t.zz[tid];
     if (tid == 0) s_bad = 0;
@@ -692,11 +729,11 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_entropy_kernel(const __grid
     }
     uint32_t* buf = p.bits + T.word0;
     const long long nwords = (long long)T.nblk * kEntropyWordsPerBlock + 1;
-    for (long long i = tid; i < nwords; i += kJpegThreads) buf[i] = 0u;
+    for (long long i = tid; i < nwords; i += kEntThreads) buf[i] = 0u;
     __syncthreads();
     const int16_t* coefs = p.coefs + T.blk0 * 64;
     unsigned long long base = 0;
-    for (int b0 = 0; b0 < T.nblk; b0 += kJpegThreads) {
+    for (int b0 = 0; b0 < T.nblk; b0 += kEntThreads) {
         const int b = b0 + tid;
         const bool mine = b < T.nblk;
         const int pred = (mine && b > 0) ? coefs[(size_t)(b - 1) * 64] : 0;
@@ -729,7 +766,7 @@ __global__ void __launch_bounds__(kJpegThreads) jpeg_entropy_kernel(const __grid
     const unsigned long long nbytes = (base + 7) >> 3;
     const long long nw = (long long)((nbytes + 3) >> 2);
     unsigned long long out_pos = 0;
-    for (long long w0 = 0; w0 < nw; w0 += kJpegThreads) {
+    for (long long w0 = 0; w0 < nw; w0 += kEntThreads) {
         const long long w = w0 + tid;
         uint32_t word = 0;
         int nb = 0, ff = 0;
@@ -765,7 +802,7 @@ void launch_jpeg_entropy_dadmm(const DadmmCodec& c, int task_begin, int task_cou
     p.hi_key = c.hi_key;
     p.N = c.N;
     p.M = c.M;
-    jpeg_entropy_kernel<<<task_count, kJpegThreads, 0, st>>>(p);
+    jpeg_entropy_kernel<<<task_count, kEntThreads, 0, st>>>(p);
     TOMO_CUDA(cudaGetLastError());
 }
 
@@ -867,7 +904,7 @@ tomo_status quant_jpeg_entropy(const int16_t* coefs, int rows, int cols, uint8_t
         p.bits = (uint32_t*)workspace;
         p.bytes = (long long*)nbytes;
         p.stream = stream;
-        jpeg_entropy_kernel<<<1, kJpegThreads, 0, (cudaStream_t)st>>>(p);
+        jpeg_entropy_kernel<<<1, kEntThreads, 0, (cudaStream_t)st>>>(p);
         TOMO_CUDA(cudaGetLastError());
     });
 }
