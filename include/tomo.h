@@ -195,6 +195,16 @@ TOMO_API tomo_status tomo_selftest_wait(tomo_geometry_t g, int timeout_ms, tomo_
 TOMO_API tomo_status tomo_fp32_peak(int target_ms, double* tflops_scalar, double* tflops_packed, double* sm_mhz,
                                     tomo_stream_t stream);
 
+/* Measured shared-memory load bandwidth of the current GPU (GB/s over all
+ * SMs): the other ceiling of both operators, which read 8 bytes of staged data
+ * from shared memory per pixel-angle update (two FP32 image values per ray and
+ * row in the projector, one (r_b, r_b+1) pair per pixel and angle in the
+ * backprojector). Conflict-free 8-byte loads (a warp reads 256 consecutive
+ * bytes) on a grid that fills every SM, timed with CUDA events over one launch
+ * of about target_ms (1..2000) after a warm-up. Synchronizes the stream;
+ * refuses a capturing stream (TOMO_ERR_INVALID_ARG). */
+TOMO_API tomo_status tomo_smem_peak(int target_ms, double* gbs, tomo_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Elementwise building blocks of the differentiable unrolled ADMM      */
 /* (Algorithm 2 step, Algorithm 3 closed form, Eq. 18; their adjoints)  */
@@ -400,13 +410,17 @@ TOMO_API tomo_status dadmm_state_init(dadmm_t h, const dadmm_state* st, tomo_str
 
 /* Report that the caller wrote the state (u, lambda, x, history or the
  * iteration counter) other than through dadmm_step / dadmm_state_init, e.g.
- * when restoring a checkpoint. The library keeps a transposed copy of u in
- * the workspace (read by the projector for steep rays) and rebuilds it at the
- * next dadmm_step only after this call, after dadmm_state_init, or when the
- * state or workspace pointers change. Host-only; never fails for a valid h. */
+ * when restoring a checkpoint. The library keeps two arrays derived from the
+ * state in the workspace: a transposed copy of u (read by the projector for
+ * steep rays) and, per node, w_m = lambda_m - rho x_m^k, the part of the
+ * Algorithm 2 step that stays fixed during its E1 inner steps (written by the
+ * dual update of the previous iteration). It rebuilds both at the next
+ * dadmm_step only after this call, after dadmm_state_init, or when the state
+ * or workspace pointers change. Host-only; never fails for a valid h. */
 TOMO_API tomo_status dadmm_state_modified(dadmm_t h);
 
-/* Scratch for dadmm_step (residuals, codec scratch, partial sums); device,
+/* Scratch for dadmm_step (residuals, the transposed copy of u and w of every
+ * node, each [S][M][N][N] float32, codec scratch, partial sums); device,
  * caller-owned, at least dadmm_workspace_size() bytes, 256-byte aligned. */
 TOMO_API size_t dadmm_workspace_size(dadmm_t h);
 

@@ -88,12 +88,13 @@ struct Dadmm {
     std::vector<int32_t> node_ang_ptr;  // [M + 1]
     // workspace layout (byte offsets from the aligned base)
     size_t off_resid = 0, off_counters = 0, off_lo = 0, off_hi = 0, off_nnz = 0, off_coefs = 0, off_bits = 0, off_dual = 0,
-           off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, ws_bytes = 0;
+           off_res = 0, off_stats = 0, off_status = 0, off_uT = 0, off_w = 0, ws_bytes = 0;
     const void* ws_status_init = nullptr;  // workspace whose status word this handle has zeroed
-    // the transposed copy of u in the workspace is current for (ut_u, ut_ws) unless ut_dirty
-    const void* ut_u = nullptr;
-    const void* ut_ws = nullptr;
-    bool ut_dirty = true;
+    // the workspace's arrays derived from the state (the transposed copy of u, and
+    // w = lambda - rho x of every node) are current for (der_u, der_ws) unless der_dirty
+    const void* der_u = nullptr;
+    const void* der_ws = nullptr;
+    bool der_dirty = true;
     // lost messages: versions held [node][segment] after iteration held_k (host), the
     // table of the current lossy call, and whether the captured graph reads it
     int max_stale = 0;
@@ -156,6 +157,7 @@ struct ElemParams {
     unsigned* lo_key;
     unsigned* hi_key;
     double* dual_part;  // [S][M*kDualPerNode][3]
+    float* w;           // [S][M][N][N] written with lambda: lambda_m^{k+1} - rho x_m^{k+1}
     int N, S, M, D, E2;
     float rho, eta2rho, inv_rho;
 };
@@ -221,7 +223,14 @@ __device__ __forceinline__ const float* view_row(const ElemParams& p, int slice,
     return p.hist + (((size_t)(j % p.D) * 3 + p.kind[mi]) * p.S + slice) * n + (size_t)i * p.N;
 }
 
-// Eq. 24 on every node: lambda_m <- lambda_m + rho (u_m - x_m^{k+1}); FP64
+// w = lambda - rho x, the part of the next Algorithm 2 step that stays fixed
+// during its inner steps (the view x^{k+1} is the one that step reads)
+__device__ __forceinline__ float4 wfix4(float4 l, float4 x, float rho) {
+    return make_float4(fmaf(-rho, x.x, l.x), fmaf(-rho, x.y, l.y), fmaf(-rho, x.z, l.z), fmaf(-rho, x.w, l.w));
+}
+
+// Eq. 24 on every node: lambda_m <- lambda_m + rho (u_m - x_m^{k+1}), and
+// w_m = lambda_m - rho x_m^{k+1} for the next iteration's Algorithm 2; FP64
 // partial norms per block (gap2 over all nodes; change and norm of node 0's view)
 __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, int node_begin, int slice_begin) {
     __shared__ double s_red[3][kElemThreads / 32];
@@ -236,6 +245,7 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
         const size_t o = ((size_t)slice * p.M + node) * n + (size_t)i * N;
         const float* u = p.u + o;
         float* l = p.lam + o;
+        float* wr = p.w + o;
         const float* x1 = view_row(p, slice, node, i, k + 1, k);
         const float* x0 = node == 0 ? view_row(p, slice, node, i, k, k) : nullptr;
         float g = 0.f, c = 0.f, q = 0.f;
@@ -272,19 +282,23 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
                 update(ua.z, xa.z, la.z, oa.z);
                 update(ua.w, xa.w, la.w, oa.w);
                 reinterpret_cast<float4*>(l)[j] = la;
+                reinterpret_cast<float4*>(wr)[j] = wfix4(la, xa, p.rho);
                 if (two) {
                     update(ub.x, xb.x, lb.x, ob.x);
                     update(ub.y, xb.y, lb.y, ob.y);
                     update(ub.z, xb.z, lb.z, ob.z);
                     update(ub.w, xb.w, lb.w, ob.w);
                     reinterpret_cast<float4*>(l)[jb] = lb;
+                    reinterpret_cast<float4*>(wr)[jb] = wfix4(lb, xb, p.rho);
                 }
             }
         } else {
             for (int j = threadIdx.x; j < N; j += kElemThreads) {
                 float lv = l[j];
-                update(u[j], x1 ? x1[j] : 0.f, lv, x0 ? x0[j] : 0.f);
+                const float xv = x1 ? x1[j] : 0.f;
+                update(u[j], xv, lv, x0 ? x0[j] : 0.f);
                 l[j] = lv;
+                wr[j] = fmaf(-p.rho, xv, lv);
             }
         }
         gap += g;
@@ -482,8 +496,8 @@ __global__ void __launch_bounds__(kElemThreads) cons_message_kernel(const ConsPa
 }
 
 // x_m^{k+1} = mean over the closed neighbourhood of the received messages;
-// lambda_m += rho (u_m - x_m^{k+1}); FP64 partial norms as dual_kernel (the
-// change and norm statistics of node 0's x)
+// lambda_m += rho (u_m - x_m^{k+1}), w_m = lambda_m - rho x_m^{k+1}; FP64
+// partial norms as dual_kernel (the change and norm statistics of node 0's x)
 __global__ void __launch_bounds__(kElemThreads) cons_dual_kernel(const ConsParams c, int node_begin, int slice_begin) {
     __shared__ double s_red[3][kElemThreads / 32];
     const ElemParams& p = c.e;
@@ -513,7 +527,9 @@ __global__ void __launch_bounds__(kElemThreads) cons_dual_kernel(const ConsParam
             c.x[o + j] = xn;
             const float pr = p.u[o + j] - xn;
             g = fmaf(pr, pr, g);
-            p.lam[o + j] = fmaf(p.rho, pr, p.lam[o + j]);
+            const float ln = fmaf(p.rho, pr, p.lam[o + j]);
+            p.lam[o + j] = ln;
+            p.w[o + j] = fmaf(-p.rho, xn, ln);
         }
         gap += g;
         chg += ch;
@@ -542,6 +558,25 @@ __global__ void __launch_bounds__(kElemThreads) cons_dual_kernel(const ConsParam
         d[0] = a;
         d[1] = b;
         d[2] = cc;
+    }
+}
+
+// w_m = lambda_m^k - rho x_m^k from the state as it is (after the state was
+// initialised or written from outside): x_m^k is the node's view of the
+// current iteration (segments variant, the relay or held version) or its own x
+// (consensus variant, xnode non-null)
+__global__ void __launch_bounds__(kElemThreads) wprep_kernel(const ElemParams p, const float* xnode) {
+    const int N = p.N;
+    const size_t n = (size_t)N * N;
+    const int k = *p.iter;
+    const long long rows = (long long)p.S * p.M * N;
+    for (long long R = blockIdx.x; R < rows; R += gridDim.x) {  // (slice * M + m) * N + i
+        const int img = (int)(R / N), i = (int)(R - (long long)img * N);
+        const int slice = img / p.M, m = img - slice * p.M;
+        const size_t o = (size_t)R * N;
+        const float* xr = xnode ? xnode + o : view_row(p, slice, m, i, k, k);
+        for (int j = threadIdx.x; j < N; j += kElemThreads)
+            p.w[o + j] = fmaf(-p.rho, xr ? xr[j] : 0.f, p.lam[o + j]);
     }
 }
 
@@ -712,6 +747,7 @@ static void build_lists(Dadmm& h) {
 
 struct WsPtrs {
     float* uT;
+    float* w;            // [S][M][N][N] lambda_m - rho x_m (the fixed part of the Algorithm 2 step)
     float* resid;
     int* counters;
     unsigned* lo;
@@ -730,6 +766,7 @@ static WsPtrs ws_ptrs(const Dadmm& h, void* ws) {
     char* b = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     WsPtrs w;
     w.uT = (float*)(b + h.off_uT);
+    w.w = (float*)(b + h.off_w);
     w.resid = (float*)(b + h.off_resid);
     w.counters = (int*)(b + h.off_counters);
     w.lo = (unsigned*)(b + h.off_lo);
@@ -761,6 +798,7 @@ static ElemParams elem_params(const Dadmm& h, const dadmm_state& st, const WsPtr
     p.lo_key = w.lo;
     p.hi_key = w.hi;
     p.dual_part = w.dual;
+    p.w = w.w;
     p.N = h.N;
     p.S = h.S;
     p.M = h.M;
@@ -807,22 +845,11 @@ static BpParams bp_params(const Dadmm& h, const dadmm_state& st, const WsPtrs& w
     bp.prescaled = 1;
     bp.pair_img = h.M;  // slice-pair items: the next slice's image of the node
     bp.pair_rows = h.A;  // ... and its residual lines
-    bp.view.hist = st.hist;
-    bp.view.iter = st.iter;
-    bp.view.lag = h.d_lag;
-    bp.view.held = h.lossy ? w.held + 4 : nullptr;
-    bp.view.k_first = h.lossy ? w.held : nullptr;
-    bp.view.kind = h.d_kind;
-    bp.view.seg_of_row = h.d_seg_of_row;
     bp.view.eta1 = h.d_eta1;
     bp.view.u = st.u;
     bp.view.uT = h.has_maps ? w.uT : nullptr;
-    bp.view.lam = st.lam;
-    bp.view.xnode = h.variant == DADMM_VARIANT_CONSENSUS ? st.xseg : nullptr;
+    bp.view.w = w.w;
     bp.view.rho = (float)h.rho;
-    bp.view.D = h.D;
-    bp.view.S = h.S;
-    bp.view.M = h.M;
     return bp;
 }
 
@@ -1292,6 +1319,7 @@ tomo_status dadmm_create(tomo_geometry_t gh, const dadmm_config* cfg, dadmm_t* o
             };
             const size_t SMn = (size_t)c.S * M;
             h->off_uT = take(sizeof(float) * (size_t)c.S * M * N * N);
+            h->off_w = take(sizeof(float) * (size_t)c.S * M * N * N);
             h->off_resid = take(sizeof(float) * (size_t)c.S * A * c.n_bins);
             h->off_counters = take(sizeof(int) * (2 * (size_t)c.E1 + 2));
             h->off_lo = take(sizeof(unsigned) * SMn);
@@ -1357,7 +1385,7 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
         TOMO_CUDA(cudaMemsetAsync(st->xseg, 0, sizeof(float) * x_values(h), s));
         TOMO_CUDA(cudaMemsetAsync(st->hist, 0, sizeof(float) * hist_values(h), s));
         TOMO_CUDA(cudaMemsetAsync(st->iter, 0, sizeof(int32_t), s));
-        h.ut_dirty = true;
+        h.der_dirty = true;
         h.held_k = -1;
     });
 }
@@ -1365,7 +1393,7 @@ tomo_status dadmm_state_init(dadmm_t hh, const dadmm_state* st, tomo_stream_t st
 tomo_status dadmm_state_modified(dadmm_t hh) {
     return guard([&] {
         Dadmm& h = *as_dadmm(hh);
-        h.ut_dirty = true;
+        h.der_dirty = true;
         h.held_k = -1;  // held versions restart from the lossless ones at the next lossy call
     });
 }
@@ -1522,7 +1550,7 @@ static void tune_shapes(Dadmm& h, const dadmm_state& st, const float* sino, cons
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        h.ut_dirty = true;  // u^T is rebuilt from u before the first iteration reads it
+        h.der_dirty = true;  // u^T is rebuilt from u before the first iteration reads it
         const int bi = (int)(std::min_element(tb.begin(), tb.begin() + bp_c.size()) - tb.begin());
         const int pi = (int)(std::min_element(tp.begin(), tp.begin() + pj_c.size()) - tp.begin());
         pick = Shape{bp_c[bi].first, bp_c[bi].second, pj_c[pi].first, pj_c[pi].second};
@@ -1620,15 +1648,20 @@ static tomo_status run_steps(dadmm_t hh, const dadmm_state* st, const float* sin
         const bool maps = build_maps();
         if (maps != (h.has_maps != 0)) h.drop_graphs();
         h.has_maps = maps ? 1 : 0;
-        auto refresh_ut = [&]() {
-            if (maps && (h.ut_dirty || h.ut_u != st->u || h.ut_ws != workspace)) {
-                launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
-                h.ut_u = st->u;
-                h.ut_ws = workspace;
-                h.ut_dirty = false;
+        auto refresh_ut = [&]() {  // u^T and w, from the state as it is
+            if (h.der_dirty || h.der_u != st->u || h.der_ws != workspace) {
+                if (maps) launch_transpose(st->u, w.uT, h.N, h.S * h.M, user);
+                const ElemParams ep = elem_params(h, *st, w);
+                const long long rows = (long long)h.S * h.M * h.N;
+                wprep_kernel<<<(int)std::min<long long>(rows, 152 * 8), kElemThreads, 0, user>>>(
+                    ep, h.variant == DADMM_VARIANT_CONSENSUS ? st->xseg : nullptr);
+                TOMO_CUDA(cudaGetLastError());
+                h.der_u = st->u;
+                h.der_ws = workspace;
+                h.der_dirty = false;
             }
         };
-        refresh_ut();  // the autotuner's projector trials read u^T too
+        refresh_ut();  // the autotuner's trials read u^T and w too
         if (!h.tuned) {
             tune_shapes(h, *st, sino, w, user);
             if (maps) build_maps();  // the chosen shape's box height

@@ -577,18 +577,6 @@ __device__ __forceinline__ void bp_issue_windows(float2* win, const BpWin* wv, i
     }
 }
 
-// row `row` of the view of x that Algorithm 2 reads for the item's node: the
-// node's own x (consensus variant), else the message-ring plane of the version
-// the node holds of the row's segment (null before any message arrived)
-__device__ __forceinline__ const float* bp_view_row(const BpView& V, const BpItem& it, int row, const int32_t* held,
-                                                    int kiter, size_t n, int N) {
-    if (V.xnode) return V.xnode + (size_t)it.img * n + (size_t)row * N;
-    const int mi = it.node * V.M + V.seg_of_row[row];
-    const int jj = held ? held[mi] : kiter - V.lag[mi];
-    return jj >= 1 ? V.hist + ((((size_t)(jj % V.D) * 3 + V.kind[mi]) * V.S + it.slice) * n) + (size_t)row * N
-                   : nullptr;
-}
-
 __device__ __forceinline__ void prefetch_l2(const void* ptr) {
     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ptr));
 }
@@ -685,13 +673,6 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
         else if (s_idx[1] < n_items) issue_consts(s_d[1], 0);
         cp_async_commit();
     }
-    int kiter = 0;
-    const int32_t* held = nullptr;  // lossy steps: the versions each node holds at this iteration
-    if (EPI == EPI_USTEP) {
-        kiter = *p.view.iter;
-        if (p.view.held) held = p.view.held + (size_t)(kiter - *p.view.k_first) * 2 * p.view.M * p.view.M;
-    }
-
     float2 acc2[SL][RPT][PX];
 #pragma unroll
     for (int sl = 0; sl < SL; ++sl)
@@ -747,23 +728,18 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
         }
         cp_async_commit();
         if (EPI == EPI_USTEP && a0 + CH >= cur.na) {
-            // the epilogue follows this chunk: bring its rows of u, lambda and the view
-            // of x into L2 now (one 128-byte line per 32 pixels of a row; a hint, no data
-            // moves to registers), so that its loads do not wait on DRAM
+            // the epilogue follows this chunk: bring its rows of u and w into L2 now
+            // (one 128-byte line per 32 pixels of a row; a hint, no data moves to
+            // registers), so that its loads do not wait on DRAM
             constexpr int LPR = TX / 32;  // lines per tile row
             static_assert(NT >= SL * LPR * kBpTileY, "one thread per line");
             const int sl = tid / (LPR * kBpTileY), t = tid - sl * (LPR * kBpTileY);
             const int row = cur.ty * kBpTileY + t / LPR;
             const int col = cur.tx * TX + 32 * (t % LPR);
             if (tid < SL * LPR * kBpTileY && row < N && col < N) {
-                BpItem cs = cur;
-                cs.img += sl * p.pair_img;
-                cs.slice += sl;
-                const size_t o = (size_t)cs.img * n + (size_t)row * N + col;
+                const size_t o = (size_t)(cur.img + sl * p.pair_img) * n + (size_t)row * N + col;
                 prefetch_l2(p.view.u + o);
-                prefetch_l2(p.view.lam + o);
-                const float* xr = bp_view_row(p.view, cs, row, held, kiter, n, N);
-                if (xr) prefetch_l2(xr + col);
+                prefetch_l2(p.view.w + o);
             }
         }
 
@@ -822,41 +798,35 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                     }
                 }
             } else {
-                // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k).
-                // Each row's view of x is located first (independent table lookups for
-                // the 4 rows).
+                // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
+                //                     = u - eta1 (P^T r + rho u + w_m),
+                // w_m = lambda_m^k - rho x_m^k being fixed during the inner steps (the dual
+                // update writes it). All of the slice's loads are issued before any update,
+                // so that their latencies overlap; pixels past the image edge load a valid
+                // neighbour and are not stored.
                 const BpView& V = p.view;
                 const float eta = V.eta1[cs.node];
                 float* u = V.u + (size_t)cs.img * n;
-                const float* lam = V.lam + (size_t)cs.img * n;
-                const float* xrow[RPT];
+                const float* wv = V.w + (size_t)cs.img * n;
+                float uo[RPT][PX], wo[RPT][PX];
 #pragma unroll
-                for (int ky = 0; ky < RPT; ++ky)
-                    xrow[ky] = bp_view_row(V, cs, min(y0 + ty + TY * ky, N - 1), held, kiter, n, N);
-                // per row: the 12 loads first, then the updates and stores (a store to u
-                // may alias a later load, so loads are not moved past stores by the compiler)
+                for (int ky = 0; ky < RPT; ++ky) {
+                    const size_t ro = (size_t)min(y0 + ty + TY * ky, N - 1) * N;
+#pragma unroll
+                    for (int kx = 0; kx < PX; ++kx) {
+                        const int col = min(x0 + tx + 16 * kx, N - 1);
+                        uo[ky][kx] = u[ro + col];
+                        wo[ky][kx] = __ldg(wv + ro + col);
+                    }
+                }
 #pragma unroll
                 for (int ky = 0; ky < RPT; ++ky) {
                     const int row = y0 + ty + TY * ky;
-                    if (row >= N) continue;
-                    float* ur = u + (size_t)row * N;
-                    const float* lr = lam + (size_t)row * N;
-                    const float* xr = xrow[ky];
-                    float uo[4], lo[4], xo[4];
 #pragma unroll
                     for (int kx = 0; kx < PX; ++kx) {
                         const int col = x0 + tx + 16 * kx;
-                        const bool ok = col < N;
-                        uo[kx] = ok ? ur[col] : 0.f;
-                        lo[kx] = ok ? __ldg(lr + col) : 0.f;
-                        xo[kx] = (ok && xr) ? __ldg(xr + col) : 0.f;
-                    }
-#pragma unroll
-                    for (int kx = 0; kx < PX; ++kx) {
-                        const int col = x0 + tx + 16 * kx;
-                        const float g = acc[ky][kx] + V.rho * (uo[kx] - xo[kx]) + lo[kx];
-                        acc[ky][kx] = uo[kx] - eta * g;
-                        if (col < N) ur[col] = acc[ky][kx];
+                        acc[ky][kx] = uo[ky][kx] - eta * (acc[ky][kx] + fmaf(V.rho, uo[ky][kx], wo[ky][kx]));
+                        if (row < N && col < N) u[(size_t)row * N + col] = acc[ky][kx];
                     }
                 }
 

@@ -229,21 +229,12 @@ struct ProjParams {
 // slice groups); false when the layout cannot be described (unaligned base, N % 4)
 bool make_image_map(CUtensorMap* map, const float* base, int N, int nimg, int rows = kProjRows);
 
-struct BpView {  // dADMM epilogue: where every node's view of x lives
-    const float* hist;        // [D][3][S][N][N]
-    const int32_t* iter;      // completed iterations k
-    const int8_t* lag;        // [M][M] (node, segment) -> relay lag
-    const int32_t* held;      // lossy steps: [iteration - *k_first][2][M][M] versions held (null: lag rule)
-    const int32_t* k_first;   // iteration of the held table's first row
-    const int8_t* kind;       // [M][M] (node, segment) -> quantizer plane
-    const int32_t* seg_of_row;  // [N]
+struct BpView {  // dADMM epilogue (Algorithm 2 step)
     const float* eta1;        // [M]
     float* u;                 // [S][M][N][N]
     float* uT;                // [S][M][N][N] transposed copy kept in step with u (may be null)
-    const float* xnode;       // consensus variant: every node's own x [S][M][N][N] (null: views)
-    const float* lam;         // [S][M][N][N]
+    const float* w;           // [S][M][N][N] lambda_m^k - rho x_m^k, fixed during the inner steps
     float rho;
-    int D, S, M;
 };
 
 struct BpParams {
