@@ -39,6 +39,9 @@ FLOP_PER_UPDATE = 8.0  # 2 touched bins x (ramp FMA + weight x value FMA)
 FP32_LANES_PER_SM = 128
 # backprojector + u-step: u, lambda, the node's view of x read; u and u^T written
 BP_BYTES_PER_PIXEL_NODE = 20.0
+# shared-memory bytes per update: two staged FP32 values (the projector's candidate
+# pixels of a row, the backprojector's (r_b, r_b+1) window pair)
+SMEM_BYTES_PER_UPDATE = 8.0
 
 
 def parse():
@@ -272,6 +275,7 @@ def run_ours(args, ws, rank, local):
         L = np.array([geo.opnorm_sq(idx[ptr[m]:ptr[m + 1]], iters=20) for m in range(prob["M"])])
     eta1 = 1.0 / (L + prob["rho"])
     fma_peak = api.fp32_peak(50)  # the FP32 roofline denominator, measured on this GPU before the run
+    smem_peak_gbs = api.smem_peak(50)  # and the shared-memory one
     sino_host = torch.as_tensor(prob["sino"]).pin_memory()
     sino = sino_host.to(dev)
     upd = updates_per_iteration(prob)
@@ -434,6 +438,13 @@ def run_ours(args, ws, rank, local):
                                            "lanes x 2 x %.0f MHz = %.1f TFLOP/s"
                                            % (fma_peak["scalar_tflops"], fma_peak["packed_tflops"],
                                               fma_peak["sm_mhz"], sms, FP32_LANES_PER_SM, sm_max, nominal_tflops),
+                             "smem": {k: {"achieved_gbs": SMEM_BYTES_PER_UPDATE * upd_per_launch / (t * 1e-3) / 1e9,
+                                          "frac": SMEM_BYTES_PER_UPDATE * upd_per_launch / (t * 1e-3) / 1e9
+                                                  / smem_peak_gbs}
+                                      for k, t in (("project", pj_ms), ("backproject_ustep", bp_ms))},
+                             "smem_peak_gbs": smem_peak_gbs,
+                             "smem_peak_basis": "measured: conflict-free 8-byte shared loads (tomo_smem_peak); "
+                                                "both operators read 8 bytes of staged data per update",
                              "hbm_frac": hbm[dominant]["frac"], "hbm_peak_gbs": hbm_peak,
                              "hbm_peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
                              "hbm": hbm,

@@ -93,6 +93,7 @@ SIGNATURES = {
     "dadmm_num_phases": (C.c_int, [C.c_void_p]),
     "dadmm_phase_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "tomo_fp32_peak": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tomo_smem_peak": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "tomo_geometry_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "tomo_geometry_cache_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -142,6 +143,14 @@ def fp32_peak(target_ms=50):
     v = (C.c_double * 3)()
     _check(lib().tomo_fp32_peak(int(target_ms), C.byref(v, 0), C.byref(v, 8), C.byref(v, 16), _stream()))
     return {"scalar_tflops": v[0], "packed_tflops": v[1], "sm_mhz": v[2]}
+
+
+def smem_peak(target_ms=50):
+    """Measured shared-memory load bandwidth of the current GPU in GB/s (tomo_smem_peak)"""
+    _require_cuda()
+    v = C.c_double()
+    _check(lib().tomo_smem_peak(int(target_ms), C.byref(v), _stream()))
+    return v.value
 
 
 def _host_i32(a):

@@ -1,14 +1,18 @@
-// Measured FP32 FMA throughput and SM clock of the current GPU: the denominator
-// of the operators' ALU roofline. The projector and the backprojector evaluate
-// the system matrix on the fly (two saturating trapezoid FMAs and one
-// accumulating FMA per touched bin), so their ceiling is the FP32 pipe, not HBM.
+// Measured FP32 FMA throughput, SM clock and shared-memory load bandwidth of the
+// current GPU: the denominators of the operators' rooflines. The projector and
+// the backprojector evaluate the system matrix on the fly (two saturating
+// trapezoid FMAs and one accumulating FMA per touched bin) from data staged in
+// shared memory, so their ceilings are the FP32 pipe and shared memory, not HBM.
 //
 // Every thread runs kPeakChains independent chains of dependent FMAs
 // a <- a * b + c (b, c kernel arguments, so nothing folds), kPeakUnroll per loop
 // trip, in scalar form (fmaf) and in packed form (__ffma2_rn, two FP32 lanes
 // per instruction); the grid fills every SM at the occupancy the API reports.
 // One thread also reads the SM cycle counter and the global nanosecond timer
-// at its start and end, which gives the SM clock the kernel ran at.
+// at its start and end, which gives the SM clock the kernel ran at. Both
+// operators read two FP32 values of shared memory per update (the staged image
+// band or the staged residual window), so the shared-memory bandwidth bounds
+// them too; its microbenchmark is below.
 #include "tomo_internal.cuh"
 
 namespace tomo {
@@ -65,6 +69,69 @@ __global__ void __launch_bounds__(kPeakThreads) fma_peak_kernel(int trips, float
         g_peak_clock[0] = (unsigned long long)(clock64() - c0);
         g_peak_clock[1] = ns_timer() - t0;
     }
+}
+
+// Shared-memory load bandwidth: every thread reads 8 float2 per loop trip at
+// addresses where a warp's 32 lanes cover 256 consecutive bytes (conflict-free:
+// two wavefronts per warp load, the layout the backprojector's window loads
+// have), moving through a 16 KB buffer so that no load can be hoisted out of
+// the loop, into 8 independent accumulators.
+constexpr int kSmemWords = kPeakThreads * 8;  // float2 entries of the buffer
+
+__global__ void __launch_bounds__(kPeakThreads) smem_peak_kernel(int trips) {
+    __shared__ float2 buf[kSmemWords];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kSmemWords; i += kPeakThreads) buf[i] = make_float2((float)i, 1.0f);
+    __syncthreads();
+    const unsigned base = (unsigned)__cvta_generic_to_shared(buf);
+    float2 acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned a = base + (unsigned)(((u * kPeakThreads + tid) + t * 32) & (kSmemWords - 1)) * 8u;
+            float x, y;
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(x), "=f"(y) : "r"(a));
+            acc[u].x += x;
+            acc[u].y += y;
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += acc[u].x + acc[u].y;
+    if (sum == -1.0f) g_peak_sink = sum;  // never: every value is >= 0
+}
+
+double run_smem_peak(int target_ms, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    TOMO_CUDA(cudaGetDevice(&dev));
+    TOMO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_peak_kernel, kPeakThreads, 0));
+    const int blocks = sms * std::max(per_sm, 1);
+    const double bytes_per_trip = 8.0 * sizeof(float2) * (double)blocks * kPeakThreads;
+    cudaEvent_t e0, e1;
+    TOMO_CUDA(cudaEventCreate(&e0));
+    TOMO_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](int trips) {
+        TOMO_CUDA(cudaEventRecord(e0, st));
+        smem_peak_kernel<<<blocks, kPeakThreads, 0, st>>>(trips);
+        TOMO_CUDA(cudaGetLastError());
+        TOMO_CUDA(cudaEventRecord(e1, st));
+        TOMO_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TOMO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return (double)ms;
+    };
+    int trips = 64;
+    timed(trips);
+    double ms = timed(trips);
+    trips = (int)std::min(16777216.0, std::max(64.0, trips * target_ms / std::max(ms, 1e-3)));
+    timed(trips);
+    ms = timed(trips);
+    TOMO_CUDA(cudaEventDestroy(e0));
+    TOMO_CUDA(cudaEventDestroy(e1));
+    return bytes_per_trip * trips / (ms * 1e-3) / 1e9;
 }
 
 struct PeakRun {
@@ -132,6 +199,18 @@ tomo_status tomo_fp32_peak(int target_ms, double* tflops_scalar, double* tflops_
         if (tflops_scalar) *tflops_scalar = s.tflops;
         if (tflops_packed) *tflops_packed = p.tflops;
         if (sm_mhz) *sm_mhz = s.mhz;
+    });
+}
+
+tomo_status tomo_smem_peak(int target_ms, double* gbs, tomo_stream_t stream) {
+    return guard([&] {
+        TOMO_REQUIRE(target_ms >= 1 && target_ms <= 2000, "target_ms must be in [1, 2000]");
+        TOMO_REQUIRE(gbs, "gbs must be non-NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        TOMO_CUDA(cudaStreamIsCapturing(st, &cap));
+        TOMO_REQUIRE(cap == cudaStreamCaptureStatusNone, "tomo_smem_peak synchronizes: not on a capturing stream");
+        *gbs = run_smem_peak(target_ms, st);
     });
 }
 

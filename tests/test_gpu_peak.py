@@ -1,7 +1,8 @@
 """The measured FP32 FMA ceiling (tomo_fp32_peak) that the benchmark divides
 the operators' achieved FLOP rate by: plausible for one GB300 (152 SMs x 128
 FP32 lanes x 2 FLOP at the measured SM clock bounds the scalar form from
-above), and refused on a stream that is capturing a CUDA graph."""
+above), the shared-memory bandwidth likewise, and refused on a stream that
+is capturing a CUDA graph."""
 import pytest
 import torch
 
@@ -37,3 +38,14 @@ def test_fp32_peak_refuses_a_capturing_stream():
             graph.capture_end()
     assert e.value.code == -1
     del graph
+
+
+def test_smem_peak_is_plausible():
+    """128 bytes per clock per SM is the shared-memory pipe's width; the
+    measured bandwidth lies between half of that and that at the measured clock"""
+    need_gpu()
+    gbs = api.smem_peak(20)
+    r = api.fp32_peak(5)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * r["sm_mhz"] * 1e6 / 1e9
+    assert 0.5 * nominal <= gbs <= 1.1 * nominal, (gbs, nominal)
