@@ -50,7 +50,7 @@ def lib():
                                             d, p, i32, i32, i32, i32, u64, p, p, p, p, p, p]),
             "orc_dadmm_iterate": (i32, [i32, i32, i32, i32, i32, p, p, p, p, p, p, p, p,
                                         d, p, d, i32, i32, i32, i32, i32, u64, i32,
-                                        p, p, p, p, p, p, p, p, p]),
+                                        p, p, p, p, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -293,9 +293,11 @@ class DADMM:
         assert self.hist.shape[0] == self.D
         self.k = int(k)
 
-    def iterate(self, sino, drop=None):
+    def iterate(self, sino, drop=None, msgs=None):
         """one iteration on sinograms [S, A, B]; returns stats [S, NSTAT].
-        drop [M, M] (s, m): node m loses owner s's message in this exchange"""
+        drop [M, M] (s, m): node m loses owner s's message in this exchange.
+        msgs [3, S, N, N]: dequantized K-means / JPEG messages to use in place
+        of the oracle's own quantizers' output (plane 0 is ignored)"""
         p = self.p
         d = _f64(sino)
         it = np.array([self.k], np.int32)
@@ -303,6 +305,9 @@ class DADMM:
         if drop is not None and self.held is None:  # the versions every node holds without losses
             self.held = np.maximum(self.k - self.lag, 0).astype(np.int32)
         dr = None if drop is None else np.ascontiguousarray(drop, np.uint8)
+        if msgs is not None:
+            mi = _f64(msgs)
+            assert mi.shape == (3, self.S, self.N, self.N)
         rc = lib().orc_dadmm_iterate(
             self.N, self.B, self.A, self.S, self.M, _ptr(self.c), _ptr(self.s),
             _ptr(self.node_ang_ptr), _ptr(self.node_ang), _ptr(self.seg_row_ptr),
@@ -310,7 +315,8 @@ class DADMM:
             float(p["rho"]), _ptr(self.eta1), float(p["eta2"]), int(p["E1"]), int(p["E2"]),
             int(p["km_k"]), int(p["km_iters"]), int(p["jpeg_quality"]), int(p["seed"]),
             self.D, _ptr(d), _ptr(self.u), _ptr(self.lam), _ptr(self.xseg), _ptr(self.hist),
-            _ptr(it), _ptr(stats), None if dr is None else _ptr(dr), None if self.held is None else _ptr(self.held))
+            _ptr(it), _ptr(stats), None if dr is None else _ptr(dr), None if self.held is None else _ptr(self.held),
+            None if msgs is None else _ptr(mi))
         if rc != 0:
             raise ValueError("orc_dadmm_iterate failed: %d" % rc)
         self.k = int(it[0])

@@ -774,7 +774,7 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       int km_k, int km_iters, int jpeg_quality, uint64_t seed,
                       int D, const double* sino, double* u, double* lam,
                       double* xseg, double* hist, int32_t* iter, double* stats,
-                      const uint8_t* drop, int32_t* held) {
+                      const uint8_t* drop, int32_t* held, const double* msg_in) {
     const long n = (long)N * N;
     if (N <= 0 || B <= 0 || M <= 0 || S <= 0 || D <= 0 || km_k > 256) return -1;
     if (seg_row_ptr[0] != 0 || seg_row_ptr[M] != N) return -1;
@@ -873,6 +873,10 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                     /* the entropy-coded blocks + (lo, hi); a constant segment is sent as lo alone */
                     const int64_t eb = (lohi[1] > lohi[0]) ? orc_jpeg_entropy(coefs, len / 64, NULL) : 0;
                     kind_bytes[q] = (double)eb + 8.0;
+                }
+                if (msg_in && q != ORC_Q_NONE) { /* the decisions supplied from outside */
+                    const double* src = msg_in + ((long)q * S + sl) * n + r0;
+                    for (long i = 0; i < len; ++i) dst[i] = src[i];
                 }
             }
             for (int t = 0; t < M; ++t)

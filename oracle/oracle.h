@@ -135,6 +135,15 @@ void orc_relay_tables(int M, const int32_t* adj, int32_t* dist, int32_t* first);
  *                            D >= max(hop distance) + 1
  *   iter  in: completed iterations k; out: k+1
  *   stats [S][ORC_NSTAT]
+ *   msg_in [3][S][N*N] or NULL: dequantized messages to use in place of the
+ *                            quantizers' output (planes ORC_Q_KMEANS and
+ *                            ORC_Q_JPEG; the identity plane is always the
+ *                            owner's own segment): Algorithm 4 with its
+ *                            discrete decisions supplied from outside, which
+ *                            separates the continuous arithmetic from the
+ *                            quantizers' decisions when two implementations
+ *                            are compared; bytes are still counted from the
+ *                            oracle's own quantizers
  * Returns 0, a negative code for invalid arguments, or -4 when a held
  * version has left the message ring (depth D). */
 int orc_dadmm_iterate(int N, int B, int A, int S, int M,
@@ -147,7 +156,7 @@ int orc_dadmm_iterate(int N, int B, int A, int S, int M,
                       int km_k, int km_iters, int jpeg_quality, uint64_t seed,
                       int D, const double* sino, double* u, double* lam,
                       double* xseg, double* hist, int32_t* iter, double* stats,
-                      const uint8_t* drop, int32_t* held);
+                      const uint8_t* drop, int32_t* held, const double* msg_in);
 
 /* Neighbour-averaged consensus (the decentralized analogue of Eq. 9; see
  * oracle.c): x [S][M][N*N] is every node's own consensus image; messages are

@@ -162,7 +162,7 @@ def test_unrolled_admm_with_64_nodes_allocates_no_work_lists_after_setup():
     backprojector call of two further forward and backward passes without
     a device allocation or free of the library's work lists"""
     need_gpu()
-    N, A, B, M = 32, 128, 47, 64
+    N, A, B, M = 64, 128, 91, 64  # one row of x per node
     p = small_problem(N=N, A=A, B=B, M=M, graph="complete", part="interleaved", noise=0.01, seed=2,
                       E1=2, E2=2)
     g = api.Geometry(N, B, p["geometry"]["theta"])

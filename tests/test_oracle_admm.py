@@ -312,3 +312,38 @@ def test_single_node_algorithm2_solves_its_subproblem_and_matches_the_iteration(
         us, _ = geo.alg2_node(u0[0, m], xk, lam0[0, m], d, sel, rho, eta[m], 3000)
         grad = geo.backproject(geo.project(us, sel) - d[sel], sel) + rho * (us - xk) + lam0[0, m]
         assert np.abs(grad).max() < 1e-9 * np.abs(lam0).max()
+
+
+def test_supplied_messages_replace_the_quantizers_output():
+    """orc_dadmm_iterate with msg_in: (a) supplying the messages the oracle's
+    own quantizers produced leaves every state bit-identical; (b) supplied
+    planes are what every node's view reads (E1 = E2 = 0, u = 0, so the dual
+    update exposes the views: lambda_m = -rho x_m^{k+1}), through the plane of
+    the path's first edge, for the segments that arrive fresh"""
+    N, M, rho = 16, 4, 2.0
+    p = small_problem(N=N, A=24, B=23, M=M, graph="ring", quant="alternate", noise=0.02, seed=4, km_k=8)
+    eta = oracle_eta1(p, iters=30)
+    a, b = O.DADMM(p, eta), O.DADMM(p, eta)
+    for _ in range(4):
+        a.iterate(p["sino"])
+        slot = a.k % a.D
+        b.iterate(p["sino"], msgs=a.hist[slot])
+        for name in ("u", "lam", "xseg", "hist"):
+            assert np.array_equal(getattr(a, name), getattr(b, name)), name
+    q = small_problem(N=N, A=24, B=23, M=M, graph="ring", quant="alternate", E1=0, E2=0, rho=rho)
+    c = O.DADMM(q, np.ones(M))
+    k = 3
+    c.load_state(np.zeros((1, M, N, N)), np.zeros((1, M, N, N)), np.ones((1, N, N)),
+                 np.zeros((c.D, 3, 1, N, N)), k)
+    msgs = np.zeros((3, 1, N, N))
+    msgs[1], msgs[2] = 11.0, 22.0  # K-means and JPEG planes
+    c.iterate(np.zeros((1, 24, 23), np.float32), msgs=msgs)
+    dist, first = O.relay_tables(q["adj"])
+    seg = q["seg_row_ptr"]
+    for m in range(M):
+        view = -c.lam[0, m] / rho
+        for s in range(M):
+            if s != m and dist[s, m] > 1:
+                continue  # relayed: an older version from the ring (zero here)
+            kind = q["home_q"][m] if s == m else q["edge_q"][s, first[s, m]]
+            assert np.all(view[seg[s]:seg[s + 1]] == (1.0, 11.0, 22.0)[kind]), (m, s)
