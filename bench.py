@@ -37,8 +37,8 @@ METRIC = "projector+backprojector GUPS and ADMM iter/s, batched vs plain on 1 GB
 UNIT = "GUPS"
 FLOP_PER_UPDATE = 8.0  # 2 touched bins x (ramp FMA + weight x value FMA)
 FP32_LANES_PER_SM = 128
-# backprojector + u-step: u, lambda, the node's view of x read; u and u^T written
-BP_BYTES_PER_PIXEL_NODE = 20.0
+# backprojector + u-step: u and w = lambda - rho x read; u and u^T written
+BP_BYTES_PER_PIXEL_NODE = 16.0
 # shared-memory bytes per update: two staged FP32 values (the projector's candidate
 # pixels of a row, the backprojector's (r_b, r_b+1) window pair)
 SMEM_BYTES_PER_UPDATE = 8.0
@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-nodes", type=int, default=64, help="oracle sample: nodes of slice 0")
+    ap.add_argument("--cpu-nodes", type=int, default=16, help="oracle sample on all cores: nodes of slice 0")
+    ap.add_argument("--cpu-nodes-one", type=int, default=1, help="oracle sample on one thread: nodes of slice 0")
     ap.add_argument("--ref-nodes", type=int, default=8, help="reference arm: nodes of slice 0 per step")
     ap.add_argument("--slices", type=int, default=None, help="override the number of slices")
     ap.add_argument("--tune", choices=["auto", "wide", "narrow", "pairs", "quads", "widepairs"], default="auto",
@@ -187,9 +188,9 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel):
-    """ncu DRAM bytes per launch from the committed summary, if it was taken on
-    the current kernel source (else None)"""
+def profile_traffic(kernel, workload):
+    """ncu DRAM bytes per launch of `kernel` on `workload` from the committed
+    summary, if it was taken on the current kernel source (else None)"""
     src = os.path.join(ROOT, "paper_2410_06106_gb300", "csrc", "operators.cu")
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -198,30 +199,67 @@ def profile_traffic(kernel):
     except (OSError, ValueError):
         return None
     e = rec.get(kernel)
-    if not e or e.get("source_sha256_16") != digest:
+    if not e or e.get("source_sha256_16") != digest or workload not in e:
         return None
-    return e.get("dram_bytes_per_launch")
+    return e[workload].get("dram_bytes_per_launch")
 
 
-def cpu_oracle_sample(prob, nodes):
-    """FP64 oracle, one Algorithm 2 inner step (P_m u, residual, P_m^T r,
-    update) for the first `nodes` nodes of slice 0; returns (updates, seconds)"""
+def cpu_oracle_sample(prob, nodes, first=0):
+    """FP64 oracle, one Algorithm 2 inner step (P_m u - d_m, P_m^T r, the update;
+    orc_alg2_node with E1 = 1) for nodes first .. first + nodes - 1 of slice 0
+    from a seeded image; returns (updates, seconds)"""
     import oracle as O
     g = prob["geometry"]
     N, B = g["N"], g["B"]
     geo = O.Geometry(N, B, g["theta"])
     rng = np.random.default_rng(5)
     u = rng.random((N, N))
+    zero = np.zeros((N, N))
+    d = np.asarray(prob["sino"][0], np.float64)
     ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
     upd = 0.0
     t0 = time.perf_counter()
-    for m in range(nodes):
+    for m in range(first, first + nodes):
         sel = idx[ptr[m]:ptr[m + 1]]
-        r = geo.project(u, sel) - prob["sino"][0][sel]
-        gr = geo.backproject(r, sel)
-        u = u - 1e-6 * (gr + 1.0 * u)
+        u, _ = geo.alg2_node(u, zero, zero, d, sel, 1.0, 1e-6, 1)
         upd += 2.0 * len(sel) * N * N
     return upd, time.perf_counter() - t0
+
+
+def cpu_baseline(prob, nodes_all, nodes_one, repeats=3):
+    """the oracle on the host cores: GUPS on all cores and on one thread, each
+    the median of `repeats` samples, and the full iteration of the workload
+    extrapolated from them (slices and inner steps are independent repeats of
+    the sampled work: time = updates / rate)"""
+    import oracle as O
+    cores = O.num_threads()
+
+    def median_rate(nodes):
+        nodes = min(nodes, prob["M"])
+        rates = []
+        for r in range(repeats):
+            u, t = cpu_oracle_sample(prob, nodes, first=(r * nodes) % (prob["M"] - nodes + 1))
+            rates.append(u / t / 1e9)
+        return float(np.median(rates))
+
+    all_cores = median_rate(nodes_all)
+    O.set_num_threads(1)
+    try:
+        one = median_rate(nodes_one)
+    finally:
+        O.set_num_threads(cores)
+    upd_iter = updates_per_iteration(prob)
+    return {"value": all_cores, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one Algorithm 2 inner step (projection, residual, backprojection, update) of %d nodes of "
+                      "slice 0 (%d on one thread), FP64 oracle; median of %d samples"
+                      % (nodes_all, nodes_one, repeats),
+            "single_thread": {"value": one, "unit": UNIT, "cores": 1},
+            "extrapolated": {"updates_per_iteration": upd_iter,
+                             "iteration_s_all_cores": upd_iter / (all_cores * 1e9),
+                             "iteration_s_one_thread": upd_iter / (one * 1e9),
+                             "stated_iterations": prob.get("iters"),
+                             "stated_run_h_all_cores": prob.get("iters", 0) * upd_iter / (all_cores * 1e9) / 3600,
+                             "basis": "updates of one iteration (2 E1 S A N^2) / the sampled rate"}}
 
 
 def run_reference(args, ws, rank):
@@ -326,11 +364,11 @@ def run_ours(args, ws, rank, local):
     nominal_tflops = sms * FP32_LANES_PER_SM * 2.0 * sm_max * 1e6 / 1e12
     peak_tflops = max(fma_peak["scalar_tflops"], fma_peak["packed_tflops"])
     achieved = FLOP_PER_UPDATE * upd_per_launch / (dom_ms * 1e-3) / 1e12
-    traffic = profile_traffic(dominant)
+    traffic = profile_traffic(dominant, args.workload if args.slices is None else None)
     # algorithmic HBM bytes per launch (4-byte values; each array once): the projector
     # reads every node's image once (u, or its transpose for steep rays) plus d and
-    # writes the residual; the backprojector + u-step reads u, lambda and the node's
-    # view of x and writes u and u^T, and reads the residual
+    # writes the residual; the backprojector + u-step reads u and w and writes u and
+    # u^T, and reads the residual
     S, M, N, A, B = prob["S"], prob["M"], g["N"], g["A"], g["B"]
     pix = float(S) * M * N * N
     bytes_launch = {"project": 4.0 * pix + 8.0 * S * A * B,
@@ -408,11 +446,7 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        import oracle as O
-        cu, ct = cpu_oracle_sample(prob, args.cpu_nodes)
-        cpu = {"value": cu / ct / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-               "sample": "one Algorithm 2 inner step of nodes 0..%d of slice 0 (%.3g updates, %.1f s)"
-                         % (args.cpu_nodes - 1, cu, ct)}
+        cpu = cpu_baseline(prob, args.cpu_nodes, args.cpu_nodes_one)
 
     # our kernels per batched iteration: E1 x (projector, backprojector), x-step, K-means and
     # JPEG (+ its entropy coder) when those messages exist, dual, residual norm, finalize

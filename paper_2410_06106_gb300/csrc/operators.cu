@@ -831,21 +831,36 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                 }
 
                 if (V.uT) {  // the transposed copy read by the projector's steep-ray items
-                    // TX x 65 floats in this chunk's stage, free once every thread is done with it
-                    static_assert(kBpTileY == 64 && 64 * 65 * 4 <= kBpStageFloat2 * 8, "transpose tile");
+                    // TX rows of 64 + 4 floats in this chunk's stage (free once every thread
+                    // is done with it): rows 16-byte aligned, so that the copy out moves
+                    // 16 bytes per load and store, 4 consecutive pixels of a column of u
+                    constexpr int TP = kBpTileY + 4;
+                    static_assert(kBpTileY == 64 && TX * TP * 4 <= kBpStageFloat2 * 8, "transpose tile");
+                    static_assert((TX * kBpTileY) % (4 * NT) == 0, "whole float4 rounds");
                     float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
                     __syncthreads();
 #pragma unroll
                     for (int ky = 0; ky < RPT; ++ky)
 #pragma unroll
-                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * 65 + ty + TY * ky] = acc[ky][kx];
+                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * TP + ty + TY * ky] = acc[ky][kx];
                     __syncthreads();
                     float* ut = V.uT + (size_t)cs.img * n;
+                    const bool vec = (N & 3) == 0;  // rows of u^T 16-byte aligned (y0 is a multiple of 64)
 #pragma unroll
-                    for (int i = 0; i < TX * kBpTileY / NT; ++i) {
+                    for (int i = 0; i < TX * kBpTileY / (4 * NT); ++i) {
                         const int e = tid + i * NT;
-                        const int cc = e >> 6, rr = e & 63;
-                        if (x0 + cc < N && y0 + rr < N) ut[(size_t)(x0 + cc) * N + y0 + rr] = T[cc * 65 + rr];
+                        const int cc = e >> 4, rq = 4 * (e & 15);  // column x0 + cc of u, rows y0 + rq .. + 3
+                        if (x0 + cc >= N) continue;
+                        const float4 v = *reinterpret_cast<const float4*>(T + cc * TP + rq);
+                        float* dst = ut + (size_t)(x0 + cc) * N + y0 + rq;
+                        if (vec && y0 + rq + 4 <= N) {
+                            *reinterpret_cast<float4*>(dst) = v;
+                        } else {  // the image's last rows (unreachable while N % 4 == 0)
+                            if (y0 + rq < N) dst[0] = v.x;
+                            if (y0 + rq + 1 < N) dst[1] = v.y;
+                            if (y0 + rq + 2 < N) dst[2] = v.z;
+                            if (y0 + rq + 3 < N) dst[3] = v.w;
+                        }
                     }
                 }
             }
