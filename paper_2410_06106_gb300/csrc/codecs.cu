@@ -124,19 +124,30 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
                 s_cnt[j * kKmThreads + tid] = 0;
             }
         double J = 0.0;
-        for (long long i = tid; i < n; i += kKmThreads) {
-            const float v = in[i];
-            const int best = nearest_centre<KMAX>(s_cent, k, v);
-            if (last) {
-                if (codes) codes[i] = (uint8_t)best;
-                deq[i] = s_cent[best];
-            } else {
-                s_sum[best * kKmThreads + tid] += __float2ll_rn(v * scale);
-                s_cnt[best * kKmThreads + tid] += 1;
-            }
-            if (obj) {
-                const double d = (double)v - (double)s_cent[best];
-                J += d * d;
+        // four consecutive values per thread and trip: four independent searches in
+        // flight hide the latency of each search's chain of shared-memory loads
+        for (long long i0 = 4ll * tid; i0 < n; i0 += 4ll * kKmThreads) {
+            float v[4];
+            int best[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = i0 + q < n ? in[i0 + q] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) best[q] = nearest_centre<KMAX>(s_cent, k, v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (i0 + q >= n) break;
+                const long long i = i0 + q;
+                if (last) {
+                    if (codes) codes[i] = (uint8_t)best[q];
+                    deq[i] = s_cent[best[q]];
+                } else {
+                    s_sum[best[q] * kKmThreads + tid] += __float2ll_rn(v[q] * scale);
+                    s_cnt[best[q] * kKmThreads + tid] += 1;
+                }
+                if (obj) {
+                    const double d = (double)v[q] - (double)s_cent[best[q]];
+                    J += d * d;
+                }
             }
         }
         if (obj) {
