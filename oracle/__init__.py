@@ -26,6 +26,7 @@ def lib():
         p = C.c_void_p
         sig = {
             "orc_num_threads": (i32, []),
+            "orc_set_num_threads": (None, [i32]),
             "orc_trig": (None, [i32, p, p, p]),
             "orc_chord": (d, [d, d, d, d, d]),
             "orc_project": (None, [i32, i32, p, p, i32, p, i32, p, p]),
@@ -34,6 +35,7 @@ def lib():
             "orc_backproject_pixels": (None, [i32, i32, p, p, i32, p, p, i32, p, p]),
             "orc_opnorm_sq": (d, [i32, i32, p, p, i32, p, i32, u64]),
             "orc_alg2_node": (d, [i32, i32, p, p, i32, p, p, p, p, d, d, i32, p]),
+            "orc_ctr": (None, [i32, i32, i32, p, p, i32, p, d, i32, p]),
             "orc_mix64": (u64, [u64]),
             "orc_kmeans_key": (u64, [u64, i32, i32, i32]),
             "orc_kmeans": (None, [p, i64, i32, i32, u64, p, p, p, p]),
@@ -77,6 +79,11 @@ def _i32(a):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """threads of the oracle's parallel loops (results do not depend on it)"""
+    lib().orc_set_num_threads(int(n))
 
 
 def trig(theta):
@@ -152,6 +159,17 @@ class Geometry:
                                   _ptr(_f64(sino)), _ptr(_f64(xview)), _ptr(_f64(lam)), float(rho),
                                   float(eta1), int(E1), _ptr(uu))
         return uu, res
+
+    def ctr(self, sino, eta, E, u0=None):
+        """Algorithm 1: E steps u <- u - eta P^T (P u - d) over every angle, from u0
+        (zero by default); sino [..., A, B] -> u [..., N, N]"""
+        d = _f64(sino)
+        lead = d.shape[:-2]
+        batch = int(np.prod(lead)) if lead else 1
+        u = np.zeros(lead + (self.N, self.N)) if u0 is None else _f64(u0).copy()
+        lib().orc_ctr(self.N, self.B, self.A, _ptr(self.c), _ptr(self.s), batch, _ptr(d), float(eta), int(E),
+                      _ptr(u))
+        return u
 
     def opnorm_sq(self, aidx=None, iters=100, seed=1):
         sel = self._sel(aidx)

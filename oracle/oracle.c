@@ -48,6 +48,14 @@ int orc_num_threads(void) {
 #endif
 }
 
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* geometry (Sec. 2.1, Eq. 1-4)                                        */
 /* ------------------------------------------------------------------ */
@@ -724,6 +732,31 @@ static void build_view(const view_ctx* v, int slice, int m, int k, const int32_t
         const double* src = v->hist + (((long)(j % v->D) * 3 + msg_kind(v, s, m)) * v->S + slice) * n;
         for (long i = r0; i < r1; ++i) out[i] = src[i];
     }
+}
+
+/* Algorithm 1 (CTR, Eq. 5): E gradient steps u <- u - eta P^T (P u - d) over
+ * every angle, from the u given (the paper starts from zero), for `batch`
+ * independent slices. u [batch][N][N] in place; sino [batch][A][B]. */
+void orc_ctr(int N, int B, int A, const double* c, const double* s, int batch, const double* sino,
+             double eta, int E, double* u) {
+    const long n = (long)N * N;
+    int32_t* all = (int32_t*)malloc(sizeof(int32_t) * (A > 0 ? A : 1));
+    for (int a = 0; a < A; ++a) all[a] = a;
+    double* r = (double*)malloc(sizeof(double) * (long)A * B);
+    double* g = (double*)malloc(sizeof(double) * n);
+    for (int k = 0; k < batch; ++k) {
+        double* uk = u + (long)k * n;
+        const double* dk = sino + (long)k * A * B;
+        for (int e = 0; e < E; ++e) {
+            orc_project(N, B, c, s, A, all, 1, uk, r); /* P u */
+            for (long i = 0; i < (long)A * B; ++i) r[i] -= dk[i]; /* - d */
+            orc_backproject(N, B, c, s, A, all, 1, r, g); /* Delta_u = P^T (P u - d) */
+            for (long i = 0; i < n; ++i) uk[i] -= eta * g[i];
+        }
+    }
+    free(all);
+    free(r);
+    free(g);
 }
 
 /* Algorithm 2 for one node: E1 gradient steps u <- u - eta1 Delta with

@@ -30,6 +30,9 @@ extern "C" {
 /* number of OpenMP threads the oracle runs with */
 int orc_num_threads(void);
 
+/* threads of the oracle's parallel loops from now on (results do not depend on it) */
+void orc_set_num_threads(int n);
+
 /* cos/sin of each angle; multiples of pi/2 (within 1e-12 rad) are snapped to
  * exact 0 / +-1. */
 void orc_trig(int n, const double* theta, double* c, double* s);
@@ -56,6 +59,13 @@ void orc_project_rays(int N, int B, const double* c, const double* s, int nray,
 void orc_backproject_pixels(int N, int B, const double* c, const double* s,
                             int nsel, const int32_t* aidx, const double* sino,
                             int npix, const int32_t* pix, double* out);
+
+/* Algorithm 1 (centralized reconstruction, Eq. 5): E steps of
+ *   u <- u - eta P^T (P u - d)
+ * over every angle, from the u given, in place; `batch` slices:
+ * u [batch][N][N], sino [batch][A][B]. */
+void orc_ctr(int N, int B, int A, const double* c, const double* s, int batch, const double* sino,
+             double eta, int E, double* u);
 
 /* Algorithm 2 for a single node m: E1 steps of
  *   u <- u - eta1 (P_m^T (P_m u - d_m) + rho (u - (x_m - lambda_m / rho)))

@@ -347,3 +347,21 @@ def test_supplied_messages_replace_the_quantizers_output():
                 continue  # relayed: an older version from the ring (zero here)
             kind = q["home_q"][m] if s == m else q["edge_q"][s, first[s, m]]
             assert np.all(view[seg[s]:seg[s + 1]] == (1.0, 11.0, 22.0)[kind]), (m, s)
+
+
+def test_ctr_first_step_and_limit():
+    """Algorithm 1 (CTR, Eq. 5): one step from zero is eta P^T d (dense
+    matrices); with eta < 2 / ||P||^2 the iteration from zero converges to the
+    minimum-norm least-squares solution (dense lstsq)"""
+    N, B, A = 8, 13, 16
+    p = small_problem(N=N, A=A, B=B, M=1, noise=0.05, seed=3)
+    geo = O.Geometry(N, B, p["geometry"]["theta"])
+    P = dense_P(geo, N)
+    d = p["sino"][0].astype(np.float64)
+    L = np.linalg.norm(P, 2) ** 2
+    eta = 1.0 / L
+    u1 = geo.ctr(d, eta, 1)
+    assert np.allclose(u1.ravel(), eta * (P.T @ d.ravel()), rtol=0, atol=1e-13 * np.abs(u1).max())
+    x_ls = np.linalg.lstsq(P, d.ravel(), rcond=None)[0]
+    u = geo.ctr(d, eta, 60000)  # condition number ~47: (1 - 1/47^2)^60000 ~ 1e-12
+    assert np.linalg.norm(u.ravel() - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
