@@ -10,7 +10,7 @@
  * iterations write disjoint outputs, so results do not depend on the thread
  * count.
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *  - geometry conventions: see oracle.h;
  *  - Algorithm 2 is warm-started from u_m^k (zero only at k = 0);
  *  - Algorithm 3 acts on the rows of segment m and is warm-started from the
