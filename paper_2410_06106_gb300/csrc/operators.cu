@@ -606,7 +606,8 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
     constexpr int TY = NT / 16;          // thread rows
     constexpr int RPT = kBpTileY / TY;   // pixel rows per thread (8, or 4 for slice pairs)
     constexpr int TX = 16 * PX;          // tile width
-    constexpr int CH = kBpChunk / SL;    // angles per chunk: a stage holds SL windows per angle
+    constexpr int CH = kBpChunk;         // angles per chunk
+    constexpr int STG = SL * CH * kBpWin;  // float2 of a stage: SL windows per angle (24 KB per slice)
     extern __shared__ __align__(16) unsigned char bp_dyn[];
     float2* wins = reinterpret_cast<float2*>(bp_dyn);  // [2][SL][CH][kBpWin]
     __shared__ BpConst s_k[CH];                        // constants of the chunk after next
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
             for (int e = tid >> 5; e < SL * nac; e += NT / 32) {
                 const int sl = SL == 1 ? 0 : e / nac, a = SL == 1 ? e : e - sl * nac;
                 const float h = s_w[buf][a].h;
-                float2* w = wins + buf * kBpStageFloat2 + (sl * CH + a) * kBpWin;
+                float2* w = wins + buf * STG + (sl * CH + a) * kBpWin;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const float2 v = w[(tid & 31) + 32 * q];
@@ -714,7 +715,7 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
         }
         if (v1) setup(it1, a1, buf ^ 1);
         __syncthreads();  // (B) the next chunk's angles are set; the constants slot is free
-        if (v1) bp_issue_windows<SL, CH, NT>(wins + (buf ^ 1) * kBpStageFloat2, s_w[buf ^ 1], min(CH, it1.na - a1), B, row_step, tid);
+        if (v1) bp_issue_windows<SL, CH, NT>(wins + (buf ^ 1) * STG, s_w[buf ^ 1], min(CH, it1.na - a1), B, row_step, tid);
         if (v2) issue_consts(s_d[j2 & 3], a2);
         if (a0 == 0 && tid < 32) {  // a new item: the descriptor three items ahead, one more queue index
             const int slot = (j + 3) & 3;
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
             }
         }
 
-        const float2* win = wins + buf * kBpStageFloat2;
+        const float2* win = wins + buf * STG;
         const BpAngle* sab = s_a[buf];
         for (int a = 0; a < nac; ++a) {
             const BpAngle& A = sab[a];
@@ -835,9 +836,9 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                     // is done with it): rows 16-byte aligned, so that the copy out moves
                     // 16 bytes per load and store, 4 consecutive pixels of a column of u
                     constexpr int TP = kBpTileY + 4;
-                    static_assert(kBpTileY == 64 && TX * TP * 4 <= kBpStageFloat2 * 8, "transpose tile");
+                    static_assert(kBpTileY == 64 && TX * TP * 4 <= STG * 8, "transpose tile");
                     static_assert((TX * kBpTileY) % (4 * NT) == 0, "whole float4 rounds");
-                    float* T = reinterpret_cast<float*>(wins + buf * kBpStageFloat2);
+                    float* T = reinterpret_cast<float*>(wins + buf * STG);
                     __syncthreads();
 #pragma unroll
                     for (int ky = 0; ky < RPT; ++ky)
@@ -964,12 +965,12 @@ void launch_project(const ProjParams& p, int grid, cudaStream_t st, int slices) 
     TOMO_CUDA(cudaGetLastError());
 }
 
-// the window stages (48 KB) and the largest shared carveout, so that four
-// blocks of each epilogue form fit on an SM; set once per process
+// the window stages (48 KB per slice of an item) and the largest shared carveout,
+// so that the blocks the launch bounds ask for fit on an SM; set once per process
 template <int EPI, int PX, int SL>
 static cudaError_t set_bp_attr() {
     cudaError_t e = cudaFuncSetAttribute(backproject_kernel<EPI, PX, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kBpSmem);
+                                         SL * kBpSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(backproject_kernel<EPI, PX, SL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
@@ -1007,9 +1008,9 @@ static void launch_bp(const BpParams& p, int grid, cudaStream_t st, int tile_x, 
     ensure_bp_attr();
     if (slices == 2) {
         if (tile_x == kBpTileXNarrow)
-            backproject_kernel<EPI, 2, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
+            backproject_kernel<EPI, 2, 2><<<grid, bp_threads(2), 2 * kBpSmem, st>>>(p);
         else
-            backproject_kernel<EPI, 4, 2><<<grid, bp_threads(2), kBpSmem, st>>>(p);
+            backproject_kernel<EPI, 4, 2><<<grid, bp_threads(2), 2 * kBpSmem, st>>>(p);
     } else if (tile_x == kBpTileXNarrow) {
         backproject_kernel<EPI, 2, 1><<<grid, kBpThreads, kBpSmem, st>>>(p);
     } else {
@@ -1047,7 +1048,7 @@ int persistent_grid_backproject(bool ustep, int tile_x, int slices) {
     int per_sm = 0;
     ensure_bp_attr();
     const void* fn = ustep ? bp_kernel_fn<EPI_USTEP>(tile_x, slices) : bp_kernel_fn<EPI_STORE>(tile_x, slices);
-    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bp_threads(slices), kBpSmem));
+    TOMO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bp_threads(slices), slices * kBpSmem));
     return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 

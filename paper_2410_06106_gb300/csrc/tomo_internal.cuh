@@ -113,8 +113,8 @@ constexpr int kProjItemBinsNarrow = 64;  // 4-angle items of the narrow shape
 constexpr int kBpChunk = 32;  // angles staged per pass
 constexpr int kBpWin = 96;    // window pairs per angle: 63 (|c| + |s|) + 6 < 96
 
-constexpr int kBpStageFloat2 = kBpChunk * kBpWin;  // one window stage; two stages in flight
-constexpr int kBpSmem = 2 * kBpStageFloat2 * (int)sizeof(float2);
+constexpr int kBpStageFloat2 = kBpChunk * kBpWin;  // one slice's window stage; two stages in flight
+constexpr int kBpSmem = 2 * kBpStageFloat2 * (int)sizeof(float2);  // per slice of an item
 
 constexpr double kFix = 1099511627776.0;  // 2^40, fixed-point scale of positions
 
