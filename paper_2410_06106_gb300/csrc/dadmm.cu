@@ -260,18 +260,20 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
         };
         if ((N & 3) == 0) {
             // rows are 16-byte aligned: two float4 of u, x and lambda per thread are
-            // loaded before any store, so the loads of a row are in flight together
+            // loaded before any store, so the loads of a row are in flight together;
+            // the node's own u, lambda and w pass through L2 once (evict-first, .cs),
+            // the views of x are shared by the nodes and keep normal priority
             const int N4 = N >> 2;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int j = threadIdx.x; j < N4; j += 2 * kElemThreads) {
                 const int jb = j + kElemThreads;
                 const bool two = jb < N4;
-                const float4 ua = __ldg(reinterpret_cast<const float4*>(u) + j);
-                const float4 ub = two ? __ldg(reinterpret_cast<const float4*>(u) + jb) : z4;
+                const float4 ua = __ldcs(reinterpret_cast<const float4*>(u) + j);
+                const float4 ub = two ? __ldcs(reinterpret_cast<const float4*>(u) + jb) : z4;
                 const float4 xa = x1 ? __ldg(reinterpret_cast<const float4*>(x1) + j) : z4;
                 const float4 xb = (x1 && two) ? __ldg(reinterpret_cast<const float4*>(x1) + jb) : z4;
-                float4 la = reinterpret_cast<const float4*>(l)[j];
-                float4 lb = two ? reinterpret_cast<const float4*>(l)[jb] : z4;
+                float4 la = __ldcs(reinterpret_cast<const float4*>(l) + j);
+                float4 lb = two ? __ldcs(reinterpret_cast<const float4*>(l) + jb) : z4;
                 float4 oa = z4, ob = z4;
                 if (node == 0 && x0) {
                     oa = __ldg(reinterpret_cast<const float4*>(x0) + j);
@@ -281,15 +283,15 @@ __global__ void __launch_bounds__(kElemThreads) dual_kernel(const ElemParams p, 
                 update(ua.y, xa.y, la.y, oa.y);
                 update(ua.z, xa.z, la.z, oa.z);
                 update(ua.w, xa.w, la.w, oa.w);
-                reinterpret_cast<float4*>(l)[j] = la;
-                reinterpret_cast<float4*>(wr)[j] = wfix4(la, xa, p.rho);
+                __stcs(reinterpret_cast<float4*>(l) + j, la);
+                __stcs(reinterpret_cast<float4*>(wr) + j, wfix4(la, xa, p.rho));
                 if (two) {
                     update(ub.x, xb.x, lb.x, ob.x);
                     update(ub.y, xb.y, lb.y, ob.y);
                     update(ub.z, xb.z, lb.z, ob.z);
                     update(ub.w, xb.w, lb.w, ob.w);
-                    reinterpret_cast<float4*>(l)[jb] = lb;
-                    reinterpret_cast<float4*>(wr)[jb] = wfix4(lb, xb, p.rho);
+                    __stcs(reinterpret_cast<float4*>(l) + jb, lb);
+                    __stcs(reinterpret_cast<float4*>(wr) + jb, wfix4(lb, xb, p.rho));
                 }
             }
         } else {

@@ -804,7 +804,9 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                 // w_m = lambda_m^k - rho x_m^k being fixed during the inner steps (the dual
                 // update writes it). All of the slice's loads are issued before any update,
                 // so that their latencies overlap; pixels past the image edge load a valid
-                // neighbour and are not stored.
+                // neighbour and are not stored. u, w and u^T stream through L2 once per
+                // launch, so they are loaded and stored evict-first (.cs), which leaves L2
+                // to the residual windows that every tile of the node re-reads.
                 const BpView& V = p.view;
                 const float eta = V.eta1[cs.node];
                 float* u = V.u + (size_t)cs.img * n;
@@ -816,8 +818,8 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
 #pragma unroll
                     for (int kx = 0; kx < PX; ++kx) {
                         const int col = min(x0 + tx + 16 * kx, N - 1);
-                        uo[ky][kx] = u[ro + col];
-                        wo[ky][kx] = __ldg(wv + ro + col);
+                        uo[ky][kx] = __ldcs(u + ro + col);
+                        wo[ky][kx] = __ldcs(wv + ro + col);
                     }
                 }
 #pragma unroll
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                     for (int kx = 0; kx < PX; ++kx) {
                         const int col = x0 + tx + 16 * kx;
                         acc[ky][kx] = uo[ky][kx] - eta * (acc[ky][kx] + fmaf(V.rho, uo[ky][kx], wo[ky][kx]));
-                        if (row < N && col < N) u[(size_t)row * N + col] = acc[ky][kx];
+                        if (row < N && col < N) __stcs(u + (size_t)row * N + col, acc[ky][kx]);
                     }
                 }
 
@@ -855,7 +857,7 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
                         const float4 v = *reinterpret_cast<const float4*>(T + cc * TP + rq);
                         float* dst = ut + (size_t)(x0 + cc) * N + y0 + rq;
                         if (vec && y0 + rq + 4 <= N) {
-                            *reinterpret_cast<float4*>(dst) = v;
+                            __stcs(reinterpret_cast<float4*>(dst), v);
                         } else {  // the image's last rows (unreachable while N % 4 == 0)
                             if (y0 + rq < N) dst[0] = v.x;
                             if (y0 + rq + 1 < N) dst[1] = v.y;
