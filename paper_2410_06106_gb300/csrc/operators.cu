@@ -772,105 +772,117 @@ __global__ void __launch_bounds__(bp_threads(SL), SL == 2 ? (PX == 4 ? 2 : 3) : 
             }
         }
 
-        if (a0 + CH >= cur.na) {  // the item's last chunk: epilogue, slice by slice
+        if (a0 + CH >= cur.na) {  // the item's last chunk: epilogue for every slice of the item
             const int x0 = cur.tx * TX, y0 = cur.ty * kBpTileY;
+            float acc[SL][RPT][PX];  // P^T r of each pixel: its two candidate bins added
 #pragma unroll
-            for (int sl = 0; sl < SL; ++sl) {
-            BpItem cs = cur;  // this slice's image and message planes
-            cs.img += sl * p.pair_img;
-            cs.slice += sl;
-            float acc[RPT][PX];
+            for (int sl = 0; sl < SL; ++sl)
 #pragma unroll
-            for (int ky = 0; ky < RPT; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < PX; ++kx) acc[ky][kx] = acc2[sl][ky][kx].x + acc2[sl][ky][kx].y;
-            if (EPI == EPI_STORE) {
-                float* img = p.img + (size_t)cs.img * n;
-#pragma unroll
-                for (int ky = 0; ky < RPT; ++ky) {
-                    const int row = y0 + ty + TY * ky;
-                    if (row >= N) continue;
+                for (int ky = 0; ky < RPT; ++ky)
 #pragma unroll
                     for (int kx = 0; kx < PX; ++kx) {
-                        const int col = x0 + tx + 16 * kx;
-                        if (col >= N) continue;
-                        float* o = img + (size_t)row * N + col;
-                        *o = (p.beta != 0.f ? *o : 0.f) + acc[ky][kx];
+                        acc[sl][ky][kx] = acc2[sl][ky][kx].x + acc2[sl][ky][kx].y;
+                        acc2[sl][ky][kx] = make_float2(0.f, 0.f);
+                    }
+            if (EPI == EPI_STORE) {
+#pragma unroll
+                for (int sl = 0; sl < SL; ++sl) {
+                    float* img = p.img + (size_t)(cur.img + sl * p.pair_img) * n;
+#pragma unroll
+                    for (int ky = 0; ky < RPT; ++ky) {
+                        const int row = y0 + ty + TY * ky;
+                        if (row >= N) continue;
+#pragma unroll
+                        for (int kx = 0; kx < PX; ++kx) {
+                            const int col = x0 + tx + 16 * kx;
+                            if (col >= N) continue;
+                            float* o = img + (size_t)row * N + col;
+                            *o = (p.beta != 0.f ? *o : 0.f) + acc[sl][ky][kx];
+                        }
                     }
                 }
             } else {
                 // Algorithm 2 step: u <- u - eta1 (P^T r + rho (u - x_m^k) + lambda_m^k)
                 //                     = u - eta1 (P^T r + rho u + w_m),
                 // w_m = lambda_m^k - rho x_m^k being fixed during the inner steps (the dual
-                // update writes it). All of the slice's loads are issued before any update,
-                // so that their latencies overlap; pixels past the image edge load a valid
-                // neighbour and are not stored. u, w and u^T stream through L2 once per
-                // launch, so they are loaded and stored evict-first (.cs), which leaves L2
-                // to the residual windows that every tile of the node re-reads.
+                // update writes it). The slices of an item belong to one node. Every load of
+                // every slice is issued before any update, so that one latency round serves
+                // the whole item; pixels past the image edge load a valid neighbour and are
+                // not stored. u, w and u^T stream through L2 once per launch, so they are
+                // loaded and stored evict-first (.cs), which leaves L2 to the residual windows
+                // that every tile of the node re-reads.
                 const BpView& V = p.view;
-                const float eta = V.eta1[cs.node];
-                float* u = V.u + (size_t)cs.img * n;
-                const float* wv = V.w + (size_t)cs.img * n;
-                float uo[RPT][PX], wo[RPT][PX];
+                const float eta = V.eta1[cur.node];
+                float uo[SL][RPT][PX], wo[SL][RPT][PX];
 #pragma unroll
-                for (int ky = 0; ky < RPT; ++ky) {
-                    const size_t ro = (size_t)min(y0 + ty + TY * ky, N - 1) * N;
+                for (int sl = 0; sl < SL; ++sl) {
+                    const size_t io = (size_t)(cur.img + sl * p.pair_img) * n;
 #pragma unroll
-                    for (int kx = 0; kx < PX; ++kx) {
-                        const int col = min(x0 + tx + 16 * kx, N - 1);
-                        uo[ky][kx] = __ldcs(u + ro + col);
-                        wo[ky][kx] = __ldcs(wv + ro + col);
+                    for (int ky = 0; ky < RPT; ++ky) {
+                        const size_t ro = io + (size_t)min(y0 + ty + TY * ky, N - 1) * N;
+#pragma unroll
+                        for (int kx = 0; kx < PX; ++kx) {
+                            const int col = min(x0 + tx + 16 * kx, N - 1);
+                            uo[sl][ky][kx] = __ldcs(V.u + ro + col);
+                            wo[sl][ky][kx] = __ldcs(V.w + ro + col);
+                        }
                     }
                 }
 #pragma unroll
-                for (int ky = 0; ky < RPT; ++ky) {
-                    const int row = y0 + ty + TY * ky;
+                for (int sl = 0; sl < SL; ++sl) {
+                    float* u = V.u + (size_t)(cur.img + sl * p.pair_img) * n;
 #pragma unroll
-                    for (int kx = 0; kx < PX; ++kx) {
-                        const int col = x0 + tx + 16 * kx;
-                        acc[ky][kx] = uo[ky][kx] - eta * (acc[ky][kx] + fmaf(V.rho, uo[ky][kx], wo[ky][kx]));
-                        if (row < N && col < N) __stcs(u + (size_t)row * N + col, acc[ky][kx]);
+                    for (int ky = 0; ky < RPT; ++ky) {
+                        const int row = y0 + ty + TY * ky;
+#pragma unroll
+                        for (int kx = 0; kx < PX; ++kx) {
+                            const int col = x0 + tx + 16 * kx;
+                            const float uk = uo[sl][ky][kx];
+                            acc[sl][ky][kx] = uk - eta * (acc[sl][ky][kx] + fmaf(V.rho, uk, wo[sl][ky][kx]));
+                            if (row < N && col < N) __stcs(u + (size_t)row * N + col, acc[sl][ky][kx]);
+                        }
                     }
                 }
 
                 if (V.uT) {  // the transposed copy read by the projector's steep-ray items
-                    // TX rows of 64 + 4 floats in this chunk's stage (free once every thread
-                    // is done with it): rows 16-byte aligned, so that the copy out moves
-                    // 16 bytes per load and store, 4 consecutive pixels of a column of u
+                    // each slice's tile as TX rows of 64 + 4 floats in this chunk's stage (free
+                    // once every thread is done with it): rows 16-byte aligned, so that the copy
+                    // out moves 16 bytes per load and store, 4 consecutive pixels of a column of u
                     constexpr int TP = kBpTileY + 4;
-                    static_assert(kBpTileY == 64 && TX * TP * 4 <= STG * 8, "transpose tile");
+                    static_assert(kBpTileY == 64 && SL * TX * TP * 4 <= STG * 8, "transpose tiles");
                     static_assert((TX * kBpTileY) % (4 * NT) == 0, "whole float4 rounds");
                     float* T = reinterpret_cast<float*>(wins + buf * STG);
                     __syncthreads();
 #pragma unroll
-                    for (int ky = 0; ky < RPT; ++ky)
+                    for (int sl = 0; sl < SL; ++sl)
 #pragma unroll
-                        for (int kx = 0; kx < PX; ++kx) T[(tx + 16 * kx) * TP + ty + TY * ky] = acc[ky][kx];
+                        for (int ky = 0; ky < RPT; ++ky)
+#pragma unroll
+                            for (int kx = 0; kx < PX; ++kx)
+                                T[sl * TX * TP + (tx + 16 * kx) * TP + ty + TY * ky] = acc[sl][ky][kx];
                     __syncthreads();
-                    float* ut = V.uT + (size_t)cs.img * n;
                     const bool vec = (N & 3) == 0;  // rows of u^T 16-byte aligned (y0 is a multiple of 64)
 #pragma unroll
-                    for (int i = 0; i < TX * kBpTileY / (4 * NT); ++i) {
-                        const int e = tid + i * NT;
-                        const int cc = e >> 4, rq = 4 * (e & 15);  // column x0 + cc of u, rows y0 + rq .. + 3
-                        if (x0 + cc >= N) continue;
-                        const float4 v = *reinterpret_cast<const float4*>(T + cc * TP + rq);
-                        float* dst = ut + (size_t)(x0 + cc) * N + y0 + rq;
-                        if (vec && y0 + rq + 4 <= N) {
-                            __stcs(reinterpret_cast<float4*>(dst), v);
-                        } else {  // the image's last rows (unreachable while N % 4 == 0)
-                            if (y0 + rq < N) dst[0] = v.x;
-                            if (y0 + rq + 1 < N) dst[1] = v.y;
-                            if (y0 + rq + 2 < N) dst[2] = v.z;
-                            if (y0 + rq + 3 < N) dst[3] = v.w;
+                    for (int sl = 0; sl < SL; ++sl) {
+                        float* ut = V.uT + (size_t)(cur.img + sl * p.pair_img) * n;
+#pragma unroll
+                        for (int i = 0; i < TX * kBpTileY / (4 * NT); ++i) {
+                            const int e = tid + i * NT;
+                            const int cc = e >> 4, rq = 4 * (e & 15);  // column x0 + cc of u, rows y0 + rq .. + 3
+                            if (x0 + cc >= N) continue;
+                            const float4 v = *reinterpret_cast<const float4*>(T + sl * TX * TP + cc * TP + rq);
+                            float* dst = ut + (size_t)(x0 + cc) * N + y0 + rq;
+                            if (vec && y0 + rq + 4 <= N) {
+                                __stcs(reinterpret_cast<float4*>(dst), v);
+                            } else {  // the image's last rows (unreachable while N % 4 == 0)
+                                if (y0 + rq < N) dst[0] = v.x;
+                                if (y0 + rq + 1 < N) dst[1] = v.y;
+                                if (y0 + rq + 2 < N) dst[2] = v.z;
+                                if (y0 + rq + 3 < N) dst[3] = v.w;
+                            }
                         }
                     }
                 }
-            }
-#pragma unroll
-            for (int ky = 0; ky < RPT; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < PX; ++kx) acc2[sl][ky][kx] = make_float2(0.f, 0.f);
             }
         }
         if (!v1) break;
