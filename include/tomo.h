@@ -235,7 +235,9 @@ TOMO_API tomo_status tomo_dot(int64_t n, const float* x, const float* y, double*
  * index, at most 64 times), sorted ascending. Then `iters` Lloyd
  * iterations: assign every value to the nearest centre by FP32 distance
  * (ties to the lower index); move each centre to the mean of its members
- * (FP64 sums, warp-shuffle reductions); empty clusters keep their centre.
+ * (exact 64-bit fixed-point sums at scale 2^sh, |v| 2^sh < 2^(62 - lg n),
+ * so that the sum does not depend on its order; the mean in FP64); empty
+ * clusters keep their centre.
  * A final assignment produces codes and deq. 1 <= k <= 32, n >= 1. */
 TOMO_API tomo_status quant_kmeans(const float* in, int64_t n, int k, int iters, uint64_t key,
                          uint8_t* codes, float* centroids, float* deq, double* objective,

@@ -23,8 +23,7 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
 // K-means
 // ------------------------------------------------------------------
 size_t kmeans_smem(int kmax) {
-    return (size_t)kmax * kKmThreads * (sizeof(double) + sizeof(int)) + kmax * sizeof(float) +
-           32 * sizeof(double);
+    return (size_t)kmax * 32 * (sizeof(long long) + sizeof(int)) + kmax * sizeof(float) + 32 * sizeof(double);
 }
 
 // Nearest centre by FP32 distance |v - c_j| with ties to the lower index, over
@@ -54,15 +53,20 @@ __device__ __forceinline__ int nearest_centre(const float* s_cent, int k, float 
 template <int KMAX>
 __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, int iters, uint64_t key,
                              uint8_t* codes, float* cent_out, float* deq, double* obj) {
+    constexpr int NT = kKmThreads, NW = kKmThreads / 32;
     extern __shared__ __align__(16) unsigned char km_smem[];
-    long long* s_sum = reinterpret_cast<long long*>(km_smem);           // [KMAX][256] fixed-point member sums
-    int* s_cnt = reinterpret_cast<int*>(s_sum + KMAX * kKmThreads);    // [KMAX][256]
-    float* s_cent = reinterpret_cast<float*>(s_cnt + KMAX * kKmThreads);
-    // 32 doubles after the centres: byte offset KMAX * (256 * 12 + 4), a multiple of 8
-    double* s_red = reinterpret_cast<double*>(km_smem + (size_t)KMAX * (kKmThreads * 12 + 4));
+    // member sums and counts: one slot per (centre, lane), shared by the block's warps
+    // (shared-memory atomic adds; lanes of one warp never share a slot)
+    unsigned long long* s_sum = reinterpret_cast<unsigned long long*>(km_smem);  // [KMAX][32]
+    int* s_cnt = reinterpret_cast<int*>(s_sum + KMAX * 32);                      // [KMAX][32]
+    float* s_cent = reinterpret_cast<float*>(s_cnt + KMAX * 32);
+    // 32 doubles after the centres: byte offset KMAX * (32 * 12 + 4), a multiple of 8
+    double* s_red = reinterpret_cast<double*>(km_smem + (size_t)KMAX * (32 * 12 + 4));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned full = 0xffffffffu;
     const uint64_t un = (uint64_t)n;
+    // 16-byte loads and stores when the segment and the output allow them (uniform per block)
+    const bool vec = (n & 3) == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)deq & 15) == 0;
 
     // Member sums are exact 64-bit fixed-point sums, scale 2^sh with
     // |v| 2^sh < 2^(62 - lg n) for every value, so that n of them fit: exact and
@@ -70,21 +74,44 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     // FP32 (a power-of-two scale); only its fraction below 2^0, i.e. below
     // 2^(lg n - 62) max|v|, is rounded away.
     float amax = 0.f;
-    for (long long i = tid; i < n; i += kKmThreads) amax = fmaxf(amax, fabsf(in[i]));
+    if (vec) {
+        const float4* in4 = reinterpret_cast<const float4*>(in);
+#pragma unroll 8
+        for (long long i = tid; i < n / 4; i += NT) {
+            const float4 a = __ldg(in4 + i);
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+        }
+    } else {
+#pragma unroll 4
+        for (long long i = tid; i < n; i += NT) amax = fmaxf(amax, fabsf(in[i]));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(full, amax, o));
     if (lane == 0) reinterpret_cast<float*>(s_red)[warp] = amax;
 
     // initial centres: value at a seeded index, moving to the next index while
-    // the value is already a centre (64 probes at most, checked 32 at a time)
+    // the value is already a centre (64 probes at most, checked 32 at a time).
+    // Every block thread first stages the probes of every centre (in the
+    // member-sum slots, free until the first iteration), so that the
+    // sequential choice below reads only shared memory.
+    float* s_probe = reinterpret_cast<float*>(s_sum);      // [k][kKmProbes]: 256 bytes per centre, as the slots
+    uint64_t* s_idx = reinterpret_cast<uint64_t*>(s_cnt);  // [k] seeded indices
+    if (tid < k) s_idx[tid] = mix64(key + (uint64_t)(tid + 1) * kGolden) % un;
+    __syncthreads();
+    for (int e = tid; e < k * kKmProbes; e += NT) {
+        const int j = e / kKmProbes, r = e - j * kKmProbes;
+        const uint64_t t = s_idx[j] + (uint64_t)r;
+        s_probe[e] = in[un > (uint64_t)kKmProbes ? (t >= un ? t - un : t) : t % un];
+    }
+    __syncthreads();
     if (warp == 0) {
         for (int j = 0; j < k; ++j) {
-            const uint64_t idx = mix64(key + (uint64_t)(j + 1) * kGolden) % un;
-            float pick = in[idx];
+            float pick = s_probe[j * kKmProbes];
             for (int round = 0; round < kKmProbes / 32; ++round) {
-                const float cand = in[(idx + (uint64_t)(round * 32 + lane)) % un];
+                const float cand = s_probe[j * kKmProbes + round * 32 + lane];
                 bool dup = false;
-                for (int q = 0; q < j; ++q) dup |= (s_cent[q] == cand);
+#pragma unroll
+                for (int q = 0; q < KMAX; ++q) dup |= (q < j) && (s_cent[q] == cand);
                 const unsigned bal = __ballot_sync(full, !dup);
                 if (bal) {
                     pick = __shfl_sync(full, cand, __ffs(bal) - 1);
@@ -94,60 +121,109 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
             if (lane == 0) s_cent[j] = pick;
             __syncwarp();
         }
-        if (lane == 0) {
-            for (int j = 1; j < k; ++j) {  // ascending order
-                const float t = s_cent[j];
-                int q = j - 1;
-                while (q >= 0 && s_cent[q] > t) {
-                    s_cent[q + 1] = s_cent[q];
-                    --q;
+        // ascending order, equal values in index order (a stable sort): each centre's
+        // rank among the k; NaN centres have no rank, so they take the insertion sort
+        const float t = lane < k ? s_cent[lane] : 0.f;
+        if (__any_sync(full, lane < k && isnan(t))) {
+            if (lane == 0) {
+                for (int j = 1; j < k; ++j) {
+                    const float u = s_cent[j];
+                    int q = j - 1;
+                    while (q >= 0 && s_cent[q] > u) {
+                        s_cent[q + 1] = s_cent[q];
+                        --q;
+                    }
+                    s_cent[q + 1] = u;
                 }
-                s_cent[q + 1] = t;
             }
-            for (int j = k; j < KMAX; ++j) s_cent[j] = INFINITY;
+        } else {
+            int rank = 0;
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q) {
+                const float cq = s_cent[q];
+                rank += (q < k && (cq < t || (cq == t && q < lane))) ? 1 : 0;
+            }
+            __syncwarp();
+            if (lane < k) s_cent[rank] = t;
         }
+        __syncwarp();
+        if (lane >= k && lane < KMAX) s_cent[lane] = INFINITY;
     }
     __syncthreads();
-    for (int w = 0; w < kKmThreads / 32; ++w) amax = fmaxf(amax, reinterpret_cast<const float*>(s_red)[w]);
+    for (int w = 0; w < NW; ++w) amax = fmaxf(amax, reinterpret_cast<const float*>(s_red)[w]);
     int lgn = 0;
     while (lgn < 62 && (1ll << lgn) < n) ++lgn;
     const int e = ((__float_as_int(amax) >> 23) & 0xff) - 126;  // amax < 2^e (e = -126 for amax = 0)
     const int sh = max(-126, min(127, 62 - lgn - e));
     const float scale = __int_as_float((sh + 127) << 23);
-    __syncthreads();  // s_red is reused below
+    __syncthreads();  // s_red, s_probe and s_idx are reused below
 
+    // four consecutive values per thread and trip; the next trip's values are
+    // loaded while this one's are assigned
+    auto load4 = [&](float (&v)[4], long long i0) {
+        if (vec) {
+            if (i0 < n) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(in + i0));
+                v[0] = a.x;
+                v[1] = a.y;
+                v[2] = a.z;
+                v[3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = i0 + q < n ? in[i0 + q] : 0.f;
+        }
+    };
     for (int t = 0; t <= iters; ++t) {
         const bool last = (t == iters);
         if (!last)
-            for (int j = 0; j < k; ++j) {
-                s_sum[j * kKmThreads + tid] = 0;
-                s_cnt[j * kKmThreads + tid] = 0;
+            for (int e = tid; e < k * 32; e += NT) {
+                s_sum[e] = 0;
+                s_cnt[e] = 0;
             }
+        __syncthreads();
         double J = 0.0;
-        // four consecutive values per thread and trip: four independent searches in
-        // flight hide the latency of each search's chain of shared-memory loads
-        for (long long i0 = 4ll * tid; i0 < n; i0 += 4ll * kKmThreads) {
+        float nv[4] = {0.f, 0.f, 0.f, 0.f};
+        load4(nv, 4ll * tid);
+        for (long long i0 = 4ll * tid; i0 < n; i0 += 4ll * NT) {
             float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = nv[q];
+            load4(nv, i0 + 4ll * NT);
             int best[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = i0 + q < n ? in[i0 + q] : 0.f;
-#pragma unroll
             for (int q = 0; q < 4; ++q) best[q] = nearest_centre<KMAX>(s_cent, k, v[q]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (i0 + q >= n) break;
-                const long long i = i0 + q;
-                if (last) {
-                    if (codes) codes[i] = (uint8_t)best[q];
-                    deq[i] = s_cent[best[q]];
+            const int nq = (int)min(4ll, n - i0);  // values of this trip (4 but at the ragged tail)
+            if (last) {
+                if (vec) {
+                    *reinterpret_cast<float4*>(deq + i0) =
+                        make_float4(s_cent[best[0]], s_cent[best[1]], s_cent[best[2]], s_cent[best[3]]);
                 } else {
-                    s_sum[best[q] * kKmThreads + tid] += __float2ll_rn(v[q] * scale);
-                    s_cnt[best[q] * kKmThreads + tid] += 1;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nq) deq[i0 + q] = s_cent[best[q]];
                 }
-                if (obj) {
-                    const double d = (double)v[q] - (double)s_cent[best[q]];
-                    J += d * d;
+                if (codes) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nq) codes[i0 + q] = (uint8_t)best[q];
                 }
+            } else {
+                // integer adds: exact, so the order in which the warps add does not matter
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nq) {
+                        atomicAdd(&s_sum[best[q] * 32 + lane], (unsigned long long)__float2ll_rn(v[q] * scale));
+                        atomicAdd(&s_cnt[best[q] * 32 + lane], 1);
+                    }
+            }
+            if (obj) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nq) {
+                        const double d = (double)v[q] - (double)s_cent[best[q]];
+                        J += d * d;
+                    }
             }
         }
         if (obj) {
@@ -157,21 +233,16 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
             __syncthreads();
             if (tid == 0) {
                 double tot = 0.0;
-                for (int w = 0; w < kKmThreads / 32; ++w) tot += s_red[w];
+                for (int w = 0; w < NW; ++w) tot += s_red[w];
                 obj[t] = tot;
             }
         }
         if (last) break;
         __syncthreads();
-        // centre update: the exact member sum over the threads' slots, mean in FP64
-        for (int j = warp; j < k; j += kKmThreads / 32) {
-            long long sm = 0;
-            int c = 0;
-#pragma unroll
-            for (int r = 0; r < kKmThreads / 32; ++r) {
-                sm += s_sum[j * kKmThreads + lane + 32 * r];
-                c += s_cnt[j * kKmThreads + lane + 32 * r];
-            }
+        // centre update: the exact member sum over the lanes' slots, mean in FP64
+        for (int j = warp; j < k; j += NW) {
+            long long sm = (long long)s_sum[j * 32 + lane];
+            int c = s_cnt[j * 32 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sm += __shfl_xor_sync(full, sm, o);
@@ -185,14 +256,14 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kKmThreads) kmeans_single_kernel(const float* in, long long n, int k,
+__global__ void __launch_bounds__(kKmThreads, 4) kmeans_single_kernel(const float* in, long long n, int k,
                                                                    int iters, uint64_t key, uint8_t* codes,
                                                                    float* cent, float* deq, double* obj) {
     kmeans_block<KMAX>(in, n, k, iters, key, codes, cent, deq, obj);
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kKmThreads) kmeans_dadmm_kernel(const DadmmCodec p, int k, int iters,
+__global__ void __launch_bounds__(kKmThreads, 4) kmeans_dadmm_kernel(const DadmmCodec p, int k, int iters,
                                                                   int task_begin) {
     const SegTask T = p.tasks[task_begin + blockIdx.x];
     const int kk = *p.iter;  // completed iterations: the messages are x^{k+1}

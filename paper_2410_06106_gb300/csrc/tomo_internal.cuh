@@ -287,7 +287,7 @@ namespace tomo {
 // ------------------------------------------------------------------
 // codecs (codecs.cu)
 // ------------------------------------------------------------------
-constexpr int kKmThreads = 256;
+constexpr int kKmThreads = 384;  // 4 blocks of 12 warps per SM (40 registers)
 constexpr int kKmMaxK = 32;
 constexpr int kKmProbes = 64;
 
