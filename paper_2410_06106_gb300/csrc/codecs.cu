@@ -23,7 +23,7 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
 // K-means
 // ------------------------------------------------------------------
 size_t kmeans_smem(int kmax) {
-    return (size_t)kmax * 32 * (sizeof(long long) + sizeof(int)) + kmax * sizeof(float) + 32 * sizeof(double);
+    return (size_t)2 * (kmax + 1) * 32 * sizeof(long long) + (kmax + 4) * sizeof(float) + 32 * sizeof(double);
 }
 
 // Nearest centre by FP32 distance |v - c_j| with ties to the lower index, over
@@ -34,18 +34,30 @@ size_t kmeans_smem(int kmax) {
 // p - 1 or p, and among equal distances on the left the lowest index is found
 // by walking down a run of equal values (only duplicate centres, or centres
 // closer together than the rounding of v - c, make that run longer than 1).
+// Without early exits: the search steps a pointer, and sentinels around the
+// centres (s_cent[-2] = s_cent[-1] = -inf, s_cent[KMAX] = +inf) let the
+// neighbours c[p - 2], c[p - 1] and c[p] load together without clamping. The
+// result is final unless `walk` is set (the first step of the walk applies:
+// duplicate or nearly equal centres); walk_down then finishes it from there.
 template <int KMAX>
-__device__ __forceinline__ int nearest_centre(const float* s_cent, int k, float v) {
-    int p = 0;
+__device__ __forceinline__ int nearest_centre_flat(const float* s_cent, int k, float v, bool& walk, float& dl) {
+    const float* c = s_cent;
 #pragma unroll
-    for (int step = KMAX / 2; step >= 1; step >>= 1)
-        if (s_cent[p + step - 1] <= v) p += step;
-    if (s_cent[p] <= v) ++p;
-    p = min(p, k);  // the +inf padding counts only for v = +inf
-    if (p == 0) return 0;
-    const float dl = v - s_cent[p - 1];
-    if (p < k && s_cent[p] - v < dl) return p;  // strict: a tie stays with the lower index
-    int best = p - 1;
+    for (int step = KMAX / 2; step >= 1; step >>= 1) c += c[step - 1] <= v ? step : 0;
+    c += c[0] <= v ? 1 : 0;
+    const int p = min((int)(c - s_cent), k);  // the +inf padding counts only for v = +inf
+    c = s_cent + p;
+    const float cm2 = c[-2], cm1 = c[-1], cp = c[0];
+    dl = v - cm1;
+    const bool up = p < k && cp - v < dl;  // strict: a tie stays with the lower index
+    const int best = p == 0 ? 0 : (up ? p : p - 1);
+    walk = !up && best > 0 && v - cm2 == dl;
+    return best;
+}
+
+// the rest of the walk, from a centre `best` whose lower neighbour is at the same distance dl
+__device__ __forceinline__ int walk_down(const float* s_cent, int best, float v, float dl) {
+    --best;
     while (best > 0 && v - s_cent[best - 1] == dl) --best;
     return best;
 }
@@ -56,15 +68,25 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     constexpr int NT = kKmThreads, NW = kKmThreads / 32;
     extern __shared__ __align__(16) unsigned char km_smem[];
     // member sums and counts: one slot per (centre, lane), shared by the block's warps
-    // (shared-memory atomic adds; lanes of one warp never share a slot)
-    unsigned long long* s_sum = reinterpret_cast<unsigned long long*>(km_smem);  // [KMAX][32]
-    int* s_cnt = reinterpret_cast<int*>(s_sum + KMAX * 32);                      // [KMAX][32]
-    float* s_cent = reinterpret_cast<float*>(s_cnt + KMAX * 32);
-    // 32 doubles after the centres: byte offset KMAX * (32 * 12 + 4), a multiple of 8
-    double* s_red = reinterpret_cast<double*>(km_smem + (size_t)KMAX * (32 * 12 + 4));
+    // (shared-memory atomic adds; lanes of one warp never share a slot). Row KMAX takes
+    // the adds of the positions past the end of a ragged last trip and is never read.
+    // Shared memory has native 32-bit atomic adds only, so a fixed-point value
+    // q = hi 2^32 + a 2^16 + b (hi = q >> 32 signed, a and b the two 16-bit halves of
+    // its low word) is added as three 32-bit pieces. A lane's slot takes at most
+    // n / 32 + 4 values per pass, so the sums of a and b stay below 2^32 for
+    // n < 2^21 - 128 and that of hi (|hi| < 2^(30 - lg n)) below 2^25; longer inputs
+    // take 64-bit slots added by compare-and-swap.
+    constexpr int CNT = (KMAX + 1) * 32;  // words (or 64-bit slots) per array
+    unsigned* s_w32 = reinterpret_cast<unsigned*>(km_smem);  // [4][KMAX + 1][32]: hi, a, b, count
+    unsigned long long* s_sum = reinterpret_cast<unsigned long long*>(km_smem);  // [KMAX + 1][32], long inputs
+    unsigned long long* s_cnt = s_sum + CNT;                                      // [KMAX + 1][32], long inputs
+    float* s_cent = reinterpret_cast<float*>(s_sum + 2 * CNT) + 2;  // [-2, KMAX]: sentinels at -2, -1, KMAX
+    // 32 doubles after the centres: byte offset 16 CNT + 4 (KMAX + 4), a multiple of 8
+    double* s_red = reinterpret_cast<double*>(km_smem + (size_t)16 * CNT + 4 * (KMAX + 4));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned full = 0xffffffffu;
     const uint64_t un = (uint64_t)n;
+    const bool split = n < (1ll << 21) - 128;  // 32-bit pieces of the member sums (below)
     // 16-byte loads and stores when the segment and the output allow them (uniform per block)
     const bool vec = (n & 3) == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)deq & 15) == 0;
 
@@ -148,6 +170,11 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
         }
         __syncwarp();
         if (lane >= k && lane < KMAX) s_cent[lane] = INFINITY;
+        if (lane == 0) {
+            s_cent[-2] = -INFINITY;
+            s_cent[-1] = -INFINITY;
+            s_cent[KMAX] = INFINITY;
+        }
     }
     __syncthreads();
     for (int w = 0; w < NW; ++w) amax = fmaxf(amax, reinterpret_cast<const float*>(s_red)[w]);
@@ -158,74 +185,116 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     const float scale = __int_as_float((sh + 127) << 23);
     __syncthreads();  // s_red, s_probe and s_idx are reused below
 
-    // four consecutive values per thread and trip; the next trip's values are
-    // loaded while this one's are assigned
-    auto load4 = [&](float (&v)[4], long long i0) {
-        if (vec) {
-            if (i0 < n) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(in + i0));
-                v[0] = a.x;
-                v[1] = a.y;
-                v[2] = a.z;
-                v[3] = a.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = i0 + q < n ? in[i0 + q] : 0.f;
-        }
-    };
     for (int t = 0; t <= iters; ++t) {
         const bool last = (t == iters);
         if (!last)
             for (int e = tid; e < k * 32; e += NT) {
-                s_sum[e] = 0;
-                s_cnt[e] = 0;
+                if (split) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) s_w32[a * CNT + e] = 0;
+                } else {
+                    s_sum[e] = 0;
+                    s_cnt[e] = 0;
+                }
             }
         __syncthreads();
         double J = 0.0;
-        float nv[4] = {0.f, 0.f, 0.f, 0.f};
-        load4(nv, 4ll * tid);
-        for (long long i0 = 4ll * tid; i0 < n; i0 += 4ll * NT) {
-            float v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = nv[q];
-            load4(nv, i0 + 4ll * NT);
-            int best[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) best[q] = nearest_centre<KMAX>(s_cent, k, v[q]);
-            const int nq = (int)min(4ll, n - i0);  // values of this trip (4 but at the ragged tail)
-            if (last) {
-                if (vec) {
-                    *reinterpret_cast<float4*>(deq + i0) =
-                        make_float4(s_cent[best[0]], s_cent[best[1]], s_cent[best[2]], s_cent[best[3]]);
+        // One assignment pass over the input, four consecutive values per thread and
+        // trip, the next trip's values loaded while this one's are assigned. The
+        // switches are compile-time: the final pass (codes and deq) or a Lloyd pass
+        // (member sums), 32-bit sum pieces with 32-bit indices, 16-byte access.
+        auto pass = [&](auto zero, auto last_c, auto split_c, auto vec_c) {
+            using I = decltype(zero);
+            constexpr bool LAST = decltype(last_c)::value, SPLIT = decltype(split_c)::value;
+            constexpr bool VEC = decltype(vec_c)::value;
+            const I ni = (I)n;
+            auto load4 = [&](float (&v)[4], I i0) {
+                if (VEC) {
+                    if (i0 < ni) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(in + i0));
+                        v[0] = a.x;
+                        v[1] = a.y;
+                        v[2] = a.z;
+                        v[3] = a.w;
+                    }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nq) deq[i0 + q] = s_cent[best[q]];
+                    for (int q = 0; q < 4; ++q) v[q] = i0 + q < ni ? in[i0 + q] : 0.f;
                 }
-                if (codes) {
+            };
+            float nv[4] = {0.f, 0.f, 0.f, 0.f};
+            load4(nv, 4 * (I)tid);
+            for (I i0 = 4 * (I)tid; i0 < ni; i0 += 4 * (I)NT) {
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = nv[q];
+                load4(nv, i0 + 4 * (I)NT);
+                int best[4];
+                bool walk[4];
+                float dl[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) best[q] = nearest_centre_flat<KMAX>(s_cent, k, v[q], walk[q], dl[q]);
+                if (walk[0] || walk[1] || walk[2] || walk[3]) {  // rare: duplicate or nearly equal centres
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (q < nq) codes[i0 + q] = (uint8_t)best[q];
+                        if (walk[q]) best[q] = walk_down(s_cent, best[q], v[q], dl[q]);
                 }
+                const int nq = VEC ? 4 : (int)min((I)4, ni - i0);  // values of this trip (4 but at a ragged tail)
+                if (LAST) {
+                    if (VEC) {
+                        *reinterpret_cast<float4*>(deq + i0) =
+                            make_float4(s_cent[best[0]], s_cent[best[1]], s_cent[best[2]], s_cent[best[3]]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nq) deq[i0 + q] = s_cent[best[q]];
+                    }
+                    if (codes) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nq) codes[i0 + q] = (uint8_t)best[q];
+                    }
+                } else {
+                    // integer adds: exact, so the order in which the warps add does not matter
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int slot = 32 * (q < nq ? best[q] : KMAX) + lane;
+                        const long long fx = __float2ll_rn(v[q] * scale);
+                        if (SPLIT) {
+                            const unsigned lo = (unsigned)fx;
+                            atomicAdd(s_w32 + slot, (unsigned)(fx >> 32));
+                            atomicAdd(s_w32 + CNT + slot, lo >> 16);
+                            atomicAdd(s_w32 + 2 * CNT + slot, lo & 0xffffu);
+                            atomicAdd(s_w32 + 3 * CNT + slot, 1u);
+                        } else {
+                            atomicAdd(s_sum + slot, (unsigned long long)fx);
+                            atomicAdd(s_cnt + slot, 1ull);
+                        }
+                    }
+                }
+                if (obj) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nq) {
+                            const double d = (double)v[q] - (double)s_cent[best[q]];
+                            J += d * d;
+                        }
+                }
+            }
+        };
+        auto run = [&](auto last_c) {
+            using T = std::true_type;
+            using F = std::false_type;
+            if (split) {  // n < 2^21: 32-bit indices as well
+                if (vec) pass(0, last_c, T{}, T{});
+                else pass(0, last_c, T{}, F{});
             } else {
-                // integer adds: exact, so the order in which the warps add does not matter
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nq) {
-                        atomicAdd(&s_sum[best[q] * 32 + lane], (unsigned long long)__float2ll_rn(v[q] * scale));
-                        atomicAdd(&s_cnt[best[q] * 32 + lane], 1);
-                    }
+                if (vec) pass(0ll, last_c, F{}, T{});
+                else pass(0ll, last_c, F{}, F{});
             }
-            if (obj) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nq) {
-                        const double d = (double)v[q] - (double)s_cent[best[q]];
-                        J += d * d;
-                    }
-            }
-        }
+        };
+        if (last) run(std::true_type{});
+        else run(std::false_type{});
         if (obj) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) J += __shfl_xor_sync(full, J, o);
@@ -241,8 +310,17 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
         __syncthreads();
         // centre update: the exact member sum over the lanes' slots, mean in FP64
         for (int j = warp; j < k; j += NW) {
-            long long sm = (long long)s_sum[j * 32 + lane];
-            int c = s_cnt[j * 32 + lane];
+            const int e = j * 32 + lane;
+            long long sm;
+            int c;
+            if (split) {
+                sm = (long long)(int)s_w32[e] * 4294967296ll + (long long)s_w32[CNT + e] * 65536ll +
+                     (long long)s_w32[2 * CNT + e];
+                c = (int)s_w32[3 * CNT + e];
+            } else {
+                sm = (long long)s_sum[e];
+                c = (int)s_cnt[e];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sm += __shfl_xor_sync(full, sm, o);
