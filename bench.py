@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--cpu-nodes-one", type=int, default=1, help="oracle sample on one thread: nodes of slice 0")
     ap.add_argument("--ref-nodes", type=int, default=8, help="reference arm: nodes of slice 0 per step")
     ap.add_argument("--slices", type=int, default=None, help="override the number of slices")
+    ap.add_argument("--n", type=int, default=None,
+                    help="override the image size N (a smaller copy of a workload, e.g. for profiling)")
+    ap.add_argument("--bins", type=int, default=None, help="override the detector bins B (with --n)")
     ap.add_argument("--tune", choices=["auto", "wide", "narrow", "pairs", "quads", "widepairs"], default="auto",
                     help="launch shapes of the operators (auto: timed at the first step)")
     ap.add_argument("--quick-eta", action="store_true",
@@ -268,7 +271,7 @@ def run_reference(args, ws, rank):
         return
     import oracle as O
     from paper_2410_06106_gb300 import synth
-    prob = synth.make_problem(args.workload, slices=1)
+    prob = synth.make_problem(args.workload, slices=1, **size_override(args))
     for _ in range(args.warmup):
         cpu_oracle_sample(prob, 1)
     tot_u, tot_t = 0.0, 0.0
@@ -283,18 +286,30 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, args.slices),
+            "data": "synthetic", "config": workload_config(args.workload, args.slices, args.n, args.bins),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(name, slices=None):
+def workload_config(name, slices=None, n=None, bins=None):
     from paper_2410_06106_gb300 import synth
     c = synth.CONFIGS[name]
-    return {"workload": name, "N": c["N"], "angles": c["A"], "bins": c["B"], "nodes": c["M"],
+    if n is not None or bins is not None:
+        name = "%s resized" % name
+    return {"workload": name, "N": n or c["N"], "angles": c["A"], "bins": bins or c["B"], "nodes": c["M"],
             "slices": slices or c["S"], "graph": "%s" % (c["graph"],), "partition": "%s" % (c["part"],),
             "quantizer": c["quant"], "E1": 10, "E2": 10, "l2": "inputs larger than L2 (no flush)"}
+
+
+def size_override(args):
+    """N and B of a smaller copy of the workload (same nodes, angles and graph)."""
+    over = {}
+    if args.n is not None:
+        over["N"] = args.n
+    if args.bins is not None:
+        over["B"] = args.bins
+    return over
 
 
 def run_ours(args, ws, rank, local):
@@ -303,7 +318,7 @@ def run_ours(args, ws, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    prob = synth.make_problem(args.workload, slices=args.slices)
+    prob = synth.make_problem(args.workload, slices=args.slices, **size_override(args))
     g = prob["geometry"]
     geo = api.Geometry(g["N"], g["B"], g["theta"])
     ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
@@ -364,7 +379,8 @@ def run_ours(args, ws, rank, local):
     nominal_tflops = sms * FP32_LANES_PER_SM * 2.0 * sm_max * 1e6 / 1e12
     peak_tflops = max(fma_peak["scalar_tflops"], fma_peak["packed_tflops"])
     achieved = FLOP_PER_UPDATE * upd_per_launch / (dom_ms * 1e-3) / 1e12
-    traffic = profile_traffic(dominant, args.workload if args.slices is None else None)
+    resized = args.slices is not None or args.n is not None or args.bins is not None
+    traffic = profile_traffic(dominant, None if resized else args.workload)
     # algorithmic HBM bytes per launch (4-byte values; each array once): the projector
     # reads every node's image once (u, or its transpose for steep rays) plus d and
     # writes the residual; the backprojector + u-step reads u and w and writes u and
@@ -458,7 +474,7 @@ def run_ours(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms_max, "iters_per_s": 1e3 / ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded random-ellipse phantoms, analytic sinograms, 1% noise)",
-                "config": dict(workload_config(args.workload, args.slices), parallelism="replicas" if ws > 1 else "single",
+                "config": dict(workload_config(args.workload, args.slices, args.n, args.bins), parallelism="replicas" if ws > 1 else "single",
                                mode="batched persistent, graph-captured",
                                launch_shape={"bp_tile_x": shape[0], "bp_slices": shape[1], "proj_item_bins": shape[2],
                                              "proj_slices": shape[3], "tune": args.tune}),

@@ -62,3 +62,24 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "GUPS" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_resized_workload_is_named_and_has_no_stress_traffic():
+    """--n / --bins build a smaller copy of a workload (for captures that must fit on the
+    device); the JSON line's config says so, and the stress shape's scaled DRAM traffic is
+    not attached to it."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    from paper_2410_06106_gb300 import synth
+    args = argparse.Namespace(n=512, bins=725)
+    assert bench.size_override(args) == {"N": 512, "B": 725}
+    assert bench.size_override(argparse.Namespace(n=None, bins=None)) == {}
+    cfg = bench.workload_config("c5_stress", 4, 512, 725)
+    assert cfg["workload"] == "c5_stress resized" and cfg["N"] == 512 and cfg["bins"] == 725
+    assert cfg["slices"] == 4 and cfg["nodes"] == synth.CONFIGS["c5_stress"]["M"]
+    full = bench.workload_config("c5_stress")
+    assert full["workload"] == "c5_stress" and full["N"] == 2048
+    prob = synth.make_problem("c5_stress", slices=1, **bench.size_override(args))
+    assert prob["geometry"]["N"] == 512 and prob["geometry"]["B"] == 725 and prob["M"] == 64
+    assert bench.profile_traffic("backproject_ustep", None) is None
