@@ -20,14 +20,19 @@ def mixture(n, k, seed):
     return (centres[rng.integers(0, k, n)] + rng.normal(0, 0.15, n)).astype(np.float32)
 
 
-@pytest.mark.parametrize("n,k,seed", [(8192, 16, 0), (65536, 32, 1), (16384, 16, 2), (1000, 3, 3),
-                                      (37, 8, 4), (5, 4, 5)])
-def test_kmeans_matches_oracle(n, k, seed):
+# The kernel adds member sums in 32-bit pieces below 2^21 - 128 values and in 64-bit slots
+# above, with 16-byte access when the input allows it (n % 4 == 0, 16-byte aligned start):
+# the cases cover both sums, both accesses and a ragged last trip.
+@pytest.mark.parametrize("n,k,seed,offset", [(8192, 16, 0, 0), (65536, 32, 1, 0), (16384, 16, 2, 0),
+                                             (1000, 3, 3, 0), (37, 8, 4, 0), (5, 4, 5, 0),
+                                             (65536, 32, 8, 1), (2097152, 32, 6, 0), (2097155, 16, 7, 1)])
+def test_kmeans_matches_oracle(n, k, seed, offset):
     need_gpu()
     v = mixture(n, max(k // 2, 2), seed)
     key = api.kmeans_key(99, 0, seed, 1)
     assert key == O.kmeans_key(99, 0, seed, 1)
-    codes, cent, deq, obj = api.quant_kmeans(cuda(v), k, 10, key, objective=True)
+    vin = cuda(np.concatenate([np.zeros(offset, np.float32), v]))[offset:]  # offset: start 4 bytes past 16
+    codes, cent, deq, obj = api.quant_kmeans(vin, k, 10, key, objective=True)
     oc, ocent, odeq, oobj = O.kmeans(v, k, 10, key)
     codes = codes.cpu().numpy().astype(int)
     diff = codes != oc
