@@ -95,6 +95,28 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     // independent of the summation order. The scaled value v 2^sh is exact in
     // FP32 (a power-of-two scale); only its fraction below 2^0, i.e. below
     // 2^(lg n - 62) max|v|, is rounded away.
+    //
+    // Initial centres: value at a seeded index, moving to the next index while
+    // the value is already a centre (64 probes at most, checked 32 at a time).
+    // Every block thread first loads the probes of every centre (they are in
+    // flight during the max|v| pass and stored to the member-sum slots, free
+    // until the first iteration, after it), so that the sequential choice below
+    // reads only shared memory.
+    float* s_probe = reinterpret_cast<float*>(s_sum);      // [k][kKmProbes]: 256 bytes per centre, as the slots
+    uint64_t* s_idx = reinterpret_cast<uint64_t*>(s_cnt);  // [k] seeded indices
+    if (tid < k) s_idx[tid] = mix64(key + (uint64_t)(tid + 1) * kGolden) % un;
+    __syncthreads();
+    constexpr int PR = (KMAX * kKmProbes + NT - 1) / NT;  // probes per thread
+    float probe[PR];
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        const int e = tid + r * NT;
+        if (e < k * kKmProbes) {
+            const int j = e / kKmProbes;
+            const uint64_t t = s_idx[j] + (uint64_t)(e - j * kKmProbes);
+            probe[r] = in[un > (uint64_t)kKmProbes ? (t >= un ? t - un : t) : t % un];
+        }
+    }
     float amax = 0.f;
     if (vec) {
         const float4* in4 = reinterpret_cast<const float4*>(in);
@@ -110,20 +132,10 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(full, amax, o));
     if (lane == 0) reinterpret_cast<float*>(s_red)[warp] = amax;
-
-    // initial centres: value at a seeded index, moving to the next index while
-    // the value is already a centre (64 probes at most, checked 32 at a time).
-    // Every block thread first stages the probes of every centre (in the
-    // member-sum slots, free until the first iteration), so that the
-    // sequential choice below reads only shared memory.
-    float* s_probe = reinterpret_cast<float*>(s_sum);      // [k][kKmProbes]: 256 bytes per centre, as the slots
-    uint64_t* s_idx = reinterpret_cast<uint64_t*>(s_cnt);  // [k] seeded indices
-    if (tid < k) s_idx[tid] = mix64(key + (uint64_t)(tid + 1) * kGolden) % un;
-    __syncthreads();
-    for (int e = tid; e < k * kKmProbes; e += NT) {
-        const int j = e / kKmProbes, r = e - j * kKmProbes;
-        const uint64_t t = s_idx[j] + (uint64_t)r;
-        s_probe[e] = in[un > (uint64_t)kKmProbes ? (t >= un ? t - un : t) : t % un];
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        const int e = tid + r * NT;
+        if (e < k * kKmProbes) s_probe[e] = probe[r];
     }
     __syncthreads();
     if (warp == 0) {
@@ -308,25 +320,34 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
         }
         if (last) break;
         __syncthreads();
-        // centre update: the exact member sum over the lanes' slots, mean in FP64
-        for (int j = warp; j < k; j += NW) {
-            const int e = j * 32 + lane;
-            long long sm;
-            int c;
-            if (split) {
-                sm = (long long)(int)s_w32[e] * 4294967296ll + (long long)s_w32[CNT + e] * 65536ll +
-                     (long long)s_w32[2 * CNT + e];
-                c = (int)s_w32[3 * CNT + e];
-            } else {
-                sm = (long long)s_sum[e];
-                c = (int)s_cnt[e];
+        // centre update: the exact member sum over the lanes' slots, mean in FP64; eight
+        // threads per centre (each adds four lanes' slots), so that every centre's
+        // division runs at once
+        static_assert(8 * KMAX <= NT, "eight threads per centre");
+        if (tid < 8 * KMAX) {
+            const int j = tid >> 3, g = tid & 7;
+            long long sm = 0;
+            int c = 0;
+            if (j < k) {
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int e = j * 32 + 4 * g + l;
+                    if (split) {
+                        sm += (long long)(int)s_w32[e] * 4294967296ll + (long long)s_w32[CNT + e] * 65536ll +
+                              (long long)s_w32[2 * CNT + e];
+                        c += (int)s_w32[3 * CNT + e];
+                    } else {
+                        sm += (long long)s_sum[e];
+                        c += (int)s_cnt[e];
+                    }
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 4; o > 0; o >>= 1) {
                 sm += __shfl_xor_sync(full, sm, o);
                 c += __shfl_xor_sync(full, c, o);
             }
-            if (lane == 0 && c > 0) s_cent[j] = (float)ldexp((double)sm / (double)c, -sh);
+            if (g == 0 && j < k && c > 0) s_cent[j] = (float)ldexp((double)sm / (double)c, -sh);
         }
         __syncthreads();
     }
