@@ -856,8 +856,8 @@ __device__ __forceinline__ void put_bits(uint32_t* buf, unsigned long long o, ui
     if ((uint32_t)x) atomicOr(buf + (o >> 5) + 1, (uint32_t)x);
 }
 
-// threads of the entropy coder's CTA: each codes one 8 x 8 block per round, so a
-// segment of 1024 blocks takes 4 rounds
+// threads of the entropy coder's CTA: each codes a contiguous run of 8 x 8 blocks
+// (4 of a 1024-block segment)
 constexpr int kEntThreads = 256;
 
 // CTA-wide exclusive scan of one value per thread (kEntThreads threads); returns the
@@ -908,31 +908,37 @@ __global__ void __launch_bounds__(kEntThreads) jpeg_entropy_kernel(const __grid_
         if (tid == 0) p.bytes[T.out] = 0;  // a constant segment is sent as its value alone
         return;
     }
+    // Each thread codes a contiguous run of blocks twice: once to size it, and,
+    // after one scan of the runs' sizes has given every run its bit offset, once to
+    // write it. Only the words the stream occupies are cleared (the rest of the
+    // buffer is never read).
     uint32_t* buf = p.bits + T.word0;
     const long long nwords = (long long)T.nblk * kEntropyWordsPerBlock + 1;
-    for (long long i = tid; i < nwords; i += kEntThreads) buf[i] = 0u;
-    __syncthreads();
     const int16_t* coefs = p.coefs + T.blk0 * 64;
-    unsigned long long base = 0;
-    for (int b0 = 0; b0 < T.nblk; b0 += kEntThreads) {
-        const int b = b0 + tid;
-        const bool mine = b < T.nblk;
-        const int pred = (mine && b > 0) ? coefs[(size_t)(b - 1) * 64] : 0;
-        int nbits = 0;
-        if (mine && !code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz,
-                                [&](uint32_t, int len) { nbits += len; }))
+    const int per = (T.nblk + kEntThreads - 1) / kEntThreads;
+    const int bb = min(T.nblk, tid * per), be = min(T.nblk, bb + per);
+    long long nbits = 0;
+    for (int b = bb; b < be; ++b) {
+        const int pred = b > 0 ? coefs[(size_t)(b - 1) * 64] : 0;
+        int nb = 0;
+        if (!code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz, [&](uint32_t, int len) { nb += len; }))
             atomicOr(&s_bad, 1);
-        long long total;
-        const unsigned long long at = base + (unsigned long long)cta_exclusive_scan(nbits, &total);
-        if (mine) {
-            unsigned long long o = at;
-            code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz, [&](uint32_t v, int len) {
-                if (len > 0) put_bits(buf, o, v, len);
-                o += len;
-            });
-        }
-        base += (unsigned long long)total;
+        nbits += nb;
     }
+    long long total;
+    const long long at = cta_exclusive_scan(nbits, &total);
+    const long long used = min((total >> 5) + 2, nwords);  // the stream and its padding
+    for (long long i = tid; i < used; i += kEntThreads) buf[i] = 0u;
+    __syncthreads();
+    unsigned long long o = (unsigned long long)at;
+    for (int b = bb; b < be; ++b) {
+        const int pred = b > 0 ? coefs[(size_t)(b - 1) * 64] : 0;
+        code_block(coefs + (size_t)b * 64, pred, s_dc, s_ac, s_zz, [&](uint32_t v, int len) {
+            if (len > 0) put_bits(buf, o, v, len);
+            o += len;
+        });
+    }
+    const unsigned long long base = (unsigned long long)total;
     if (tid == 0 && (base & 7)) {  // pad the last byte with 1-bits
         const int pad = 8 - (int)(base & 7);
         put_bits(buf, base, (1u << pad) - 1u, pad);
@@ -947,6 +953,19 @@ __global__ void __launch_bounds__(kEntThreads) jpeg_entropy_kernel(const __grid_
     const unsigned long long nbytes = (base + 7) >> 3;
     const long long nw = (long long)((nbytes + 3) >> 2);
     unsigned long long out_pos = 0;
+    if (!p.stream) {  // the byte count only: one reduction over the words
+        long long cnt = 0;
+        for (long long w = tid; w < nw; w += kEntThreads) {
+            const uint32_t word = __ldcg(buf + w);
+            const int nb = (int)min(4ull, nbytes - 4ull * (unsigned long long)w);
+            cnt += nb;
+            for (int q = 0; q < nb; ++q) cnt += ((word >> (24 - 8 * q)) & 255u) == 255u;
+        }
+        long long all;
+        cta_exclusive_scan(cnt, &all);
+        if (tid == 0) p.bytes[T.out] = all;
+        return;
+    }
     for (long long w0 = 0; w0 < nw; w0 += kEntThreads) {
         const long long w = w0 + tid;
         uint32_t word = 0;
