@@ -70,12 +70,13 @@ __device__ void kmeans_block(const float* __restrict__ in, long long n, int k, i
     // member sums and counts: one slot per (centre, lane), shared by the block's warps
     // (shared-memory atomic adds; lanes of one warp never share a slot). Row KMAX takes
     // the adds of the positions past the end of a ragged last trip and is never read.
-    // Shared memory has native 32-bit atomic adds only, so a fixed-point value
-    // q = hi 2^32 + a 2^16 + b (hi = q >> 32 signed, a and b the two 16-bit halves of
-    // its low word) is added as three 32-bit pieces. A lane's slot takes at most
-    // n / 32 + 4 values per pass, so the sums of a and b stay below 2^32 for
-    // n < 2^21 - 128 and that of hi (|hi| < 2^(30 - lg n)) below 2^25; longer inputs
-    // take 64-bit slots added by compare-and-swap.
+    // Shared memory has native 32-bit atomic adds only (64-bit adds are compare-and-swap
+    // loops), so a fixed-point value q = hi 2^32 + a 2^16 + b (hi = q >> 32 signed, a
+    // and b the two 16-bit halves of its low word) is added as three 32-bit pieces, with
+    // a 32-bit count. A lane's slot takes at most min(n, n / 32 + 4) values per pass, so
+    // the sums of a and b stay below 2^32 for n < 2^21 - 128, and that of hi
+    // (|hi| < 2^(30 - lg n), at most n <= 2^lg n of them) below 2^30; longer inputs take
+    // 64-bit slots added by compare-and-swap.
     constexpr int CNT = (KMAX + 1) * 32;  // words (or 64-bit slots) per array
     unsigned* s_w32 = reinterpret_cast<unsigned*>(km_smem);  // [4][KMAX + 1][32]: hi, a, b, count
     unsigned long long* s_sum = reinterpret_cast<unsigned long long*>(km_smem);  // [KMAX + 1][32], long inputs
