@@ -172,3 +172,28 @@ def test_entropy_coding_refuses_out_of_range_coefficients():
     c[0, 1] = 1024
     with pytest.raises(api.TomoError):
         api.jpeg_entropy(torch.as_tensor(c).cuda(), 8, 8)
+
+
+@pytest.mark.parametrize("n,k,kind", [(65536, 8, "halves"), (65536, 32, "halves"), (65536, 32, "zeros"),
+                                      (4099, 16, "halves"), (65536, 16, "magnitudes")])
+def test_kmeans_duplicates_and_exact_ties_match_oracle(n, k, kind):
+    """Inputs that stress the decision rule: few distinct values (multiples of 1/2 in
+    [-3, 3], so that values fall exactly halfway between centres and, with k above
+    the 13 distinct values, centres repeat); mostly zeros; magnitudes over seven
+    decades. Codes, centres and dequantized values follow the oracle (Algorithm 5)."""
+    need_gpu()
+    rng = np.random.default_rng(n + k)
+    if kind == "halves":
+        v = (rng.integers(-6, 7, n) * 0.5).astype(np.float32)
+    elif kind == "zeros":
+        v = np.where(rng.random(n) < 0.7, 0.0, rng.normal(0, 1, n)).astype(np.float32)
+    else:
+        v = (rng.standard_normal(n) * 10.0 ** rng.integers(-3, 4, n)).astype(np.float32)
+    key = api.kmeans_key(7, 1, k, 2)
+    codes, cent, deq, _ = api.quant_kmeans(cuda(v), k, 10, key)
+    oc, ocent, odeq, _ = O.kmeans(v, k, 10, key)
+    codes = codes.cpu().numpy().astype(int)
+    diff = codes != oc
+    assert diff.mean() <= 1e-4 and np.all(np.abs(codes[diff] - oc[diff]) <= 1)
+    assert rel_l2(cent.cpu().numpy(), ocent) <= 1e-6
+    assert rel_l2(deq.cpu().numpy(), odeq) <= 1e-5
