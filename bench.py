@@ -220,6 +220,7 @@ def cpu_oracle_sample(prob, nodes, first=0):
     zero = np.zeros((N, N))
     d = np.asarray(prob["sino"][0], np.float64)
     ptr, idx = prob["node_ang_ptr"], prob["node_ang"]
+    nodes = min(nodes, prob["M"] - first)  # the problem may have fewer nodes than asked for
     upd = 0.0
     t0 = time.perf_counter()
     for m in range(first, first + nodes):
@@ -255,7 +256,7 @@ def cpu_baseline(prob, nodes_all, nodes_one, repeats=3):
     return {"value": all_cores, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "one Algorithm 2 inner step (projection, residual, backprojection, update) of %d nodes of "
                       "slice 0 (%d on one thread), FP64 oracle; median of %d samples"
-                      % (nodes_all, nodes_one, repeats),
+                      % (min(nodes_all, prob["M"]), min(nodes_one, prob["M"]), repeats),
             "single_thread": {"value": one, "unit": UNIT, "cores": 1},
             "extrapolated": {"updates_per_iteration": upd_iter,
                              "iteration_s_all_cores": upd_iter / (all_cores * 1e9),
@@ -274,15 +275,16 @@ def run_reference(args, ws, rank):
     prob = synth.make_problem(args.workload, slices=1, **size_override(args))
     for _ in range(args.warmup):
         cpu_oracle_sample(prob, 1)
+    nodes = min(args.ref_nodes, prob["M"])
     tot_u, tot_t = 0.0, 0.0
     for _ in range(args.steps):
-        u, t = cpu_oracle_sample(prob, args.ref_nodes)
+        u, t = cpu_oracle_sample(prob, nodes)
         tot_u += u
         tot_t += t
     v = tot_u / tot_t / 1e9
     cores = O.num_threads()
     sample = ("one Algorithm 2 inner step (projection, residual, backprojection, update) of nodes 0..%d of "
-              "slice 0 per step, FP64 oracle, %d OpenMP threads" % (args.ref_nodes - 1, cores))
+              "slice 0 per step, FP64 oracle, %d OpenMP threads" % (nodes - 1, cores))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

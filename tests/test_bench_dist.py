@@ -83,3 +83,15 @@ def test_resized_workload_is_named_and_has_no_stress_traffic():
     prob = synth.make_problem("c5_stress", slices=1, **bench.size_override(args))
     assert prob["geometry"]["N"] == 512 and prob["geometry"]["B"] == 725 and prob["M"] == 64
     assert bench.profile_traffic("backproject_ustep", None) is None
+
+
+def test_reference_arm_on_a_problem_with_fewer_nodes_than_sampled():
+    """the reference arm samples --ref-nodes nodes (8 by default); a problem with fewer
+    (c1_tiny has 4) is sampled whole instead of failing"""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "c1_tiny", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([x for x in out.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert "nodes 0..3 " in line["cpu_baseline"]["sample"]
