@@ -1,9 +1,9 @@
 // Message quantizers of dADMM-K and dADMM-J (Sec. 2.7) on GB300:
-//   - scalar K-means (Algorithm 5): one CTA per vector, warp-parallel seeded
-//     initialisation, FP32 nearest-centre decisions by binary search over the
-//     sorted centres, exact 64-bit fixed-point centroid sums kept per thread
-//     in shared memory and combined with warp shuffles (order-independent,
-//     so deterministic), means in FP64;
+//   - scalar K-means (Algorithm 5): one CTA per vector, seeded initialisation
+//     from probes staged in shared memory, FP32 nearest-centre decisions by
+//     binary search over the sorted centres, exact 64-bit fixed-point centroid
+//     sums in one shared slot per (centre, lane) added with 32-bit shared
+//     atomics (integer sums: order-independent, so deterministic), means in FP64;
 //   - JPEG-style codec: one thread per 8x8 block, the orthonormal DCT-II and
 //     its inverse separable in registers on the FP32 cores, luminance table
 //     of ITU-T T.81 Annex K scaled by the IJG quality rule.
